@@ -1,0 +1,481 @@
+#!/usr/bin/env python
+"""Benchmark: batched NTT polynomial products over Z/pZ on GB300.
+
+Workload (one step): 256 independent products mod p = 3*2^30+1 of two
+length-2^15 operands with residues uniform in [0, p) (seeded), through
+size-2^16 transforms: two forward transforms, pointwise product, inverse
+transform (Section 5.2 of van der Hoeven-Lecerf-Quintin).  The fused
+schedule is the measured value; the one-launch-per-radix-2-stage schedule
+("plain") is measured beside it on the same inputs.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle
+(schoolbook, OpenMP over coefficients) on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "batched NTT polymul products/s and GB/s (% of HBM peak), batched vs plain"
+UNIT = "products/s"
+WORKLOAD = {"workload": "256 products mod 3*2^30+1, operands 2^15 uint32, size-2^16 NTTs",
+            "p": 3221225473, "batch": 256, "na": 1 << 15, "nb": 1 << 15, "log2n": 16,
+            "word": "u32"}
+SM_COUNT = 152
+INT_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+L2_BYTES = 129 * 1024 * 1024
+
+# 32-bit-instruction counts of the word policy's arithmetic (Mont32, any odd
+# p < 2^32): modular add, subtract, fixed-multiplicand product, general
+# (Montgomery) product.
+OPS32 = {"add": 4, "sub": 3, "mulw": 6, "mulg": 7}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- algorithmic counts
+
+def dif_counts(L: int):
+    """(nontrivial, trivial) radix-2 butterflies of a length-L transform."""
+    k = L.bit_length() - 1
+    total = (L // 2) * k
+    trivial = L - 1
+    return total - trivial, trivial
+
+
+def fused_kernel_ops(log2n: int, na: int, nb: int, batch: int, tile_max_log: int):
+    """Algorithmic 32-bit integer operations per launch of each fused kernel."""
+    o = OPS32
+    N = 1 << log2n
+    nc = na + nb - 1
+
+    def transform_ops(L):
+        nt, tr = dif_counts(L)
+        return nt * (o["add"] + o["sub"] + o["mulw"]) + tr * (o["add"] + o["sub"])
+
+    if log2n <= tile_max_log:
+        per = 3 * transform_ops(N) + N * o["mulg"] + nc * o["mulw"]
+        return {"k_tile_polymul": per * batch}
+    k2 = log2n // 2
+    k1 = log2n - k2
+    n1, n2 = 1 << k1, 1 << k2
+    step2 = (N - n1 - n2 + 1) * o["mulw"]
+    col_fwd = 2 * (n1 * transform_ops(n2) + step2)
+    row = 3 * n2 * transform_ops(n1) + N * o["mulg"]
+    col_inv = step2 + n1 * transform_ops(n2) + nc * o["mulw"]
+    return {"k_col_fwd": col_fwd * batch, "k_row_polymul": row * batch,
+            "k_col_inv": col_inv * batch}
+
+
+def alg_bytes(na, nb, batch, wb):
+    return batch * (na + nb + (na + nb - 1)) * wb
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[4:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, flags in rows:
+            for nm, fl in zip(names, flags[1:]):
+                if fl.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def reduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def whole_job_value(products_per_rank: int, world: int, max_seconds: float) -> float:
+    """Weak scaling: every rank runs the full workload; whole-job rate is the
+    units all ranks processed over the slowest rank's time."""
+    return products_per_rank * world / max_seconds
+
+
+# ---------------------------------------------------------------- inputs
+
+def make_inputs():
+    from paper_1407_3383_gb300 import workloads as W
+    p, a, b = W.config1()
+    return p, a, b
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1407_3383_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        data = json.load(open(path))
+    except Exception:
+        return None
+    ent = data.get(kernel)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+# ---------------------------------------------------------------- CPU oracle timing
+
+def time_oracle(p, a, b, target_s: float = 12.0):
+    """The oracle's schoolbook product on a bounded sample of the workload's
+    products, on this host's cores.  Returns (products/s, cores, sample text)."""
+    import numpy as np
+    import oracle as O
+    cores = O.num_threads()
+    # calibrate on one product, then size the sample to about target_s
+    t0 = time.perf_counter()
+    O.polymul_batch(p, a[:1].astype(np.uint64), b[:1].astype(np.uint64))
+    one = time.perf_counter() - t0
+    count = int(max(1, min(a.shape[0], target_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    O.polymul_batch(p, a[:count].astype(np.uint64), b[:count].astype(np.uint64))
+    dt = time.perf_counter() - t0
+    sample = (f"{count} of the {a.shape[0]} products (schoolbook, all {a.shape[1] + b.shape[1] - 1} "
+              f"coefficients each), {dt:.1f} s wall on {cores} threads")
+    return count / dt, cores, sample
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    p, a, b = make_inputs()
+    import numpy as np
+    import oracle as O
+    cores = O.num_threads()
+    per_step = 4
+    for _ in range(max(0, args.warmup)):
+        O.polymul_batch(p, a[:1].astype(np.uint64), b[:1].astype(np.uint64))
+    times = []
+    for s in range(args.steps):
+        i0 = (s * per_step) % a.shape[0]
+        aa = a[i0:i0 + per_step].astype(np.uint64)
+        bb = b[i0:i0 + per_step].astype(np.uint64)
+        t0 = time.perf_counter()
+        O.polymul_batch(p, aa, bb)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": dict(WORKLOAD, timed_sample=f"{per_step} products per step"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} of 256 products per step, schoolbook, "
+                                   f"{args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- native timing
+
+def timed_steps(step, flush, steps, stream):
+    """Per-step device time with CUDA events on the launching stream; the L2
+    flush between steps is outside the events."""
+    import torch
+    evs = []
+    for _ in range(steps):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def profile_window(G, step, flush, steps):
+    """Run `steps` steps with launch profiling on; returns per-kernel lists of ms."""
+    import ctypes
+    import torch
+    lib = G.lib()
+    lib.ntt_profile_begin.restype = ctypes.c_int
+    lib.ntt_profile_end.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                    ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int)]
+    per = {}
+    launches = 0
+    for _ in range(steps):
+        flush()
+        torch.cuda.synchronize()
+        lib.ntt_profile_begin()
+        step()
+        cap = 256
+        ms = (ctypes.c_float * cap)()
+        names = (ctypes.c_char_p * cap)()
+        cnt = ctypes.c_int()
+        rc = lib.ntt_profile_end(cap, ms, names, ctypes.byref(cnt))
+        assert rc == 0
+        launches += cnt.value
+        for i in range(min(cnt.value, cap)):
+            per.setdefault(names[i].decode(), []).append(ms[i])
+    return per, launches / max(1, steps)
+
+
+def run_native(args, world, rank, local):
+    import numpy as np
+    import torch
+    import paper_1407_3383_gb300 as G
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    p, a, b = make_inputs()
+    batch, na = a.shape
+    nb = b.shape[1]
+    nc = na + nb - 1
+    log2n = WORKLOAD["log2n"]
+    plan = G.Plan(p, log2n, G.NTT_FLAG_PLAIN)
+    wb = plan.word_bytes
+    da = torch.from_numpy(a.reshape(-1)).to(dev)
+    db = torch.from_numpy(b.reshape(-1)).to(dev)
+    dc = torch.empty(batch * nc, dtype=torch.uint32, device=dev)
+    ws_f = G.alloc_workspace(plan, batch, G.NTT_SCHED_FUSED)
+    ws_p = G.alloc_workspace(plan, batch, G.NTT_SCHED_PLAIN)
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def flush():
+        flush_buf.fill_(1)
+
+    def step_fused():
+        G.polymul_mod_p_batch(plan, da, na, db, nb, batch, dc, G.NTT_SCHED_FUSED, ws_f,
+                              stream=stream)
+
+    def step_plain():
+        G.polymul_mod_p_batch(plan, da, na, db, nb, batch, dc, G.NTT_SCHED_PLAIN, ws_p,
+                              stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step_fused()
+        step_plain()
+    torch.cuda.synchronize()
+
+    # ---- fused: the reported value
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    ms = timed_steps(step_fused, flush, args.steps, stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    total_s = reduce_max(sum(ms) / 1e3, world)
+    value = whole_job_value(batch, world, total_s / args.steps)
+    ms_per_step = 1e3 * total_s / args.steps
+
+    # ---- per-kernel device time (launch profiling, same steps)
+    per_kernel, launches_per_step = profile_window(G, step_fused, flush, max(5, args.steps // 4))
+    kops = fused_kernel_ops(log2n, na, nb, batch, plan.info.tile_max_log)
+    shares = {k: sum(v) for k, v in per_kernel.items()}
+    dom = max(shares, key=shares.get)
+    dom_ms = statistics.mean(per_kernel[dom])
+    dom_ops = kops.get(dom, 0)
+    sm_mhz = clk["sm_mhz"] or SM_MAX_MHZ
+    peak_gops = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
+    achieved_gops = dom_ops / (dom_ms * 1e-3) / 1e9
+
+    # ---- plain schedule, same inputs
+    psteps = args.plain_steps or max(3, args.steps // 4)
+    pms = timed_steps(step_plain, flush, psteps, stream)
+    plain_s = reduce_max(sum(pms) / 1e3, world)
+    plain_value = whole_job_value(batch, world, plain_s / psteps)
+
+    # ---- end to end: pinned host buffers, copies inside the timed region
+    ha = torch.from_numpy(a.reshape(-1)).pin_memory()
+    hb = torch.from_numpy(b.reshape(-1)).pin_memory()
+    hc = torch.empty(batch * nc, dtype=torch.uint32).pin_memory()
+    e2e_steps = max(3, args.steps // 4)
+
+    def step_e2e():
+        G.polymul_mod_p_batch_host(plan, ha, na, hb, nb, batch, hc, da, db, dc, ws_f,
+                                   stream=stream)
+
+    for _ in range(2):
+        step_e2e()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    e2e_value = whole_job_value(batch, world, e2e_s / e2e_steps)
+
+    # int-pipe probe (context for the roofline)
+    probe = {}
+    import ctypes
+    lib = G.lib()
+    for kind, name in [(0, "imad"), (1, "iadd_lop")]:
+        out = ctypes.c_double()
+        lib.ntt_int_probe.argtypes = [ctypes.c_uint, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+        if lib.ntt_int_probe(kind, SM_COUNT * 8, 256, 4096, stream.cuda_stream,
+                             ctypes.byref(out)) == 0:
+            probe[name + "_gops"] = round(out.value / 1e9, 1)
+
+    bytes_step = alg_bytes(na, nb, batch, wb)
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs") \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    gbps = bytes_step / (ms_per_step * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cv, cores, sample = time_oracle(p, a, b)
+        cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank != 0:
+        plan.close()
+        return
+    traffic = ncu_traffic(dom)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": dict(WORKLOAD, l2="flushed between timed steps (256 MiB write)",
+                       schedule="fused", parallelism=f"replicas x{world}"),
+        "gbps_algorithmic": gbps,
+        "hbm_frac_of_measured": gbps / hbm,
+        "plain": {"value": plain_value, "ms_per_step": 1e3 * plain_s / psteps,
+                  "fused_over_plain": value / plain_value},
+        "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops,
+                     "unit": "Gop/s", "frac": achieved_gops / peak_gops, "traffic": traffic,
+                     "kernel": dom, "kernel_ms": dom_ms,
+                     "peak_basis": "152 SMs x 128 int32 lanes x 2070 MHz (unit counts and max clock)",
+                     "int_probe": probe},
+        "kernels": {k: {"ms_mean": statistics.mean(v), "share": shares[k] / sum(shares.values()),
+                        "alg_gop_per_launch": kops.get(k, 0) / 1e9} for k, v in per_kernel.items()},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": (na + nb) * batch * wb,
+                "d2h_bytes_per_step": nc * batch * wb},
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_native(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * gbntt.h -- C ABI of the GB300 modular NTT library (libgbntt.so).
+ *
+ * Exact number-theoretic transforms over F_p, p = k 2^l + 1 a word-size
+ * prime, and the products built on them, after van der Hoeven, Lecerf and
+ * Quintin, "Modular SIMD arithmetic in Mathemagix" (2014):
+ *   - the transform FFT_w / TFT_w of Section 5.1 (Algorithm 1),
+ *   - the polynomial product over Z/pZ of Section 5.2,
+ *   - the three-prime integer product of Section 5.3.
+ *
+ * Conventions for every call:
+ *   - Residues are stored as their representative in {0, ..., p-1}
+ *     (Section 2).  Words are uint32_t when p < 2^32, uint64_t when
+ *     2^32 <= p < 2^62; a plan reports which (word_bytes).
+ *   - Pointers named d_* are caller-owned DEVICE memory; h_* are host
+ *     memory.  The library never frees or keeps caller buffers.  Inputs are
+ *     never modified, except by the in-place transforms.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device calls are asynchronous on that stream; an OK return
+ *     means the work was enqueued.  Errors detected on the host return
+ *     before anything is enqueued.
+ *   - Every call returns an int status: NTT_OK (0) or an NTT_ERR_* code;
+ *     ntt_status_str() names it and ntt_last_error() gives details for the
+ *     calling thread.
+ *   - A plan is immutable after creation and may be shared across threads
+ *     and streams.  Hot calls allocate nothing: calls that need scratch
+ *     memory take a caller workspace whose size the *_workspace_size
+ *     queries return.
+ */
+#ifndef GBNTT_H
+#define GBNTT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum ntt_status {
+    NTT_OK = 0,
+    NTT_ERR_ARG = 1,          /* null pointer, bad flag or enum value */
+    NTT_ERR_MODULUS = 2,      /* p even, p < 3, p >= 2^62, or 16 does not divide p-1 */
+    NTT_ERR_NOT_PRIME = 3,    /* p is not prime */
+    NTT_ERR_NO_ROOT = 4,      /* 2^log2n does not divide p - 1 */
+    NTT_ERR_SIZE = 5,         /* sizes exceed what the plan supports */
+    NTT_ERR_RANGE = 6,        /* an input residue is >= p (NTT_FLAG_CHECK only) */
+    NTT_ERR_OOM = 7,          /* device or host allocation failed */
+    NTT_ERR_TIMEOUT = 8,      /* a bounded device wait expired */
+    NTT_ERR_CUDA = 9,         /* a CUDA runtime call failed */
+    NTT_ERR_WORKSPACE = 10,   /* workspace missing or too small */
+    NTT_ERR_UNSUPPORTED = 11  /* valid request this build does not implement */
+};
+
+/* Plan creation flags. */
+#define NTT_FLAG_PLAIN 0x1u   /* also build the tables of the one-launch-per-stage schedule */
+#define NTT_FLAG_CHECK 0x2u   /* validate input ranges on the host side of each call */
+
+/* Schedules for polymul_mod_p_batch. */
+#define NTT_SCHED_FUSED 0u    /* Algorithm 1 passes fused in shared memory */
+#define NTT_SCHED_PLAIN 1u    /* one kernel launch per radix-2 stage (baseline) */
+
+/* Modular-product variants for ntt_modmul_vec (Sections 2.2, 2.3, 3.3). */
+#define NTT_MM_BARRETT 0u     /* Function 6 on the full product x*y, Table 3 parameters */
+#define NTT_MM_SHOUP 1u       /* Function 8: y fixed, companion psi = floor(2^n y / p) */
+#define NTT_MM_MONTGOMERY 2u  /* Function 13 on x~ y~ (inputs in Montgomery form) */
+#define NTT_MM_FMA 3u         /* Function 16 over IEEE double, p < 2^50 */
+#define NTT_MM_MONT_FIXED 4u  /* Remark 8: y fixed, companion phi; kernels' twiddle product */
+#define NTT_MM_MONT_PRODUCT 5u /* the kernels' general (pointwise) product: x y 2^-n rem p, scaled back */
+
+typedef struct ntt_plan ntt_plan;
+
+typedef struct ntt_plan_info {
+    uint64_t p;           /* the modulus */
+    uint64_t g;           /* least generator of F_p^* */
+    uint64_t omega;       /* primitive n-th root used: g^((p-1)/n) */
+    uint64_t omega_inv;   /* omega^-1 rem p */
+    uint64_t n_inv;       /* n^-1 rem p */
+    uint32_t log2n;       /* n = 2^log2n */
+    uint32_t word_bytes;  /* 4 or 8 */
+    uint32_t v2;          /* largest l with 2^l | p - 1 */
+    uint32_t tile_max_log;/* largest log2n transformed by one thread block */
+} ntt_plan_info;
+
+/* ---- host-only planning (no GPU needed) -------------------------------- */
+
+/* The index-th (0-based) prime p = k 2^min_l + 1 with 2^(bits-1) < p < 2^bits,
+ * by ascending k (Section 1: moduli p = k 2^l + 1 with l large).
+ * bits in [3, 63], min_l < bits - 1.  Writes *p_out.
+ * NTT_ERR_ARG on bad arguments, NTT_ERR_SIZE if the window holds fewer
+ * than index+1 such primes. */
+int ntt_find_prime(unsigned bits, unsigned min_l, unsigned index, uint64_t* p_out);
+
+/* The least generator g of F_p^* and omega = g^((p-1)/2^log2n), the
+ * primitive 2^log2n-th root of unity every transform of this library uses
+ * (Section 5.1 requires a primitive n-th root; this fixes which one).
+ * NTT_ERR_NOT_PRIME, NTT_ERR_NO_ROOT as for ntt_plan_create. */
+int ntt_root_of_unity(uint64_t p, unsigned log2n, uint64_t* g_out, uint64_t* omega_out);
+
+/* Host computation of the fixed-multiplicand companions for ntt_modmul_vec,
+ * for words of n = 8 * word_bytes bits: kind NTT_MM_SHOUP: out[i] =
+ * floor(2^n y[i] / p) (Function 8's psi); NTT_MM_MONT_FIXED (n = 32 only):
+ * out[i] = (y[i] 2^32 rem p) p^-1 rem 2^32 (Remark 8's companion of the
+ * Montgomery form).  Host buffers; y[i] are reduced mod p first. */
+int ntt_fixed_companion(uint64_t p, unsigned kind, unsigned word_bytes, const uint64_t* h_y,
+                        uint64_t* h_out, size_t n);
+
+/* ---- plans ------------------------------------------------------------- */
+
+/* Create a plan for transforms of length n = 2^log2n over F_p on the
+ * current CUDA device: checks p (prime, odd, < 2^62, 16 | p-1) and
+ * 2^log2n | p-1, builds the root-of-unity tables on the host (Section 5.1:
+ * all powers precomputed and cached) and copies them to the device once.
+ * 1 <= log2n <= 24.  flags: NTT_FLAG_*.  The plan owns its device tables;
+ * free it with ntt_plan_destroy.  Errors: NTT_ERR_ARG, NTT_ERR_MODULUS,
+ * NTT_ERR_NOT_PRIME, NTT_ERR_NO_ROOT, NTT_ERR_SIZE, NTT_ERR_OOM, NTT_ERR_CUDA. */
+int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_plan** out);
+
+/* Free the plan and its device tables (synchronises the plan's device). */
+int ntt_plan_destroy(ntt_plan* plan);
+
+/* Fill *out with the plan's parameters. */
+int ntt_plan_get_info(const ntt_plan* plan, ntt_plan_info* out);
+
+/* ---- transforms ---------------------------------------------------------- */
+
+/* In-place forward transform of `batch` vectors of n words stored back to
+ * back at d_data: vector v becomes TFT_omega with l = n (Section 5.1),
+ * i.e. word i holds A(omega^[i]) where [i] mirrors the log2n bits of i.
+ * Inputs must be residues < p. */
+int ntt_forward(const ntt_plan* plan, void* d_data, size_t batch, void* stream);
+
+/* In-place inverse: consumes the bit-mirrored order ntt_forward produces and
+ * returns natural order scaled by n^-1, so ntt_inverse(ntt_forward(a)) = a
+ * (the inverse of Algorithm 1, text after Proposition 15). */
+int ntt_inverse(const ntt_plan* plan, void* d_data, size_t batch, void* stream);
+
+/* ---- polynomial products over Z/pZ (Section 5.2) ---------------------- */
+
+/* Workspace bytes polymul_mod_p_batch needs for `batch` products with this
+ * plan and schedule (0 when none is needed). */
+size_t polymul_workspace_size(const ntt_plan* plan, size_t batch, unsigned schedule);
+
+/* c = a * b over Z/pZ for `batch` independent pairs: a is batch x na words,
+ * b is batch x nb words, c is batch x (na + nb - 1) words, all row-major and
+ * back to back.  Requires 1 <= na, nb and na + nb - 1 <= n: the product is
+ * the size-n cyclic convolution of the zero-padded operands, which equals the
+ * linear product when no coefficient wraps.  Two forward transforms, the
+ * pointwise product and one inverse transform (Section 5.2).  schedule:
+ * NTT_SCHED_FUSED or NTT_SCHED_PLAIN (the latter needs NTT_FLAG_PLAIN).
+ * d_ws: at least polymul_workspace_size bytes, 256-byte aligned (may be
+ * NULL when that size is 0). */
+int polymul_mod_p_batch(const ntt_plan* plan, const void* d_a, size_t na,
+                        const void* d_b, size_t nb, size_t batch, void* d_c,
+                        unsigned schedule, void* d_ws, size_t ws_bytes, void* stream);
+
+/* The single-product form of polymul_mod_p_batch (fused schedule). */
+int polymul_mod_p(const ntt_plan* plan, const void* d_a, size_t na, const void* d_b,
+                  size_t nb, void* d_c, void* d_ws, size_t ws_bytes, void* stream);
+
+/* ---- element-wise modular products (Sections 2.2, 2.3, 3.3) ----------- */
+
+/* z[i] = x[i] * y[i] rem p with the reduction `kind` (NTT_MM_*), on uint64
+ * device arrays of residues < p.  word_bytes selects the 32- or 64-bit
+ * implementation (4 needs p < 2^32).  NTT_MM_SHOUP / NTT_MM_MONT_FIXED read
+ * the companions d_yc (from ntt_fixed_companion); other kinds ignore it.
+ * NTT_MM_MONTGOMERY converts x, y to Montgomery form, multiplies with
+ * Function 13 and converts back.  NTT_MM_FMA needs p < 2^50. */
+int ntt_modmul_vec(uint64_t p, unsigned kind, unsigned word_bytes, const uint64_t* d_x,
+                   const uint64_t* d_y, const uint64_t* d_yc, uint64_t* d_z, size_t n,
+                   void* stream);
+
+/* ---- diagnostics --------------------------------------------------------- */
+
+/* Launch profiling (the paper has no counterpart; it reports CPU user time
+ * per transform, Section 5.1).  After ntt_profile_begin(), every library
+ * call records a CUDA event on its own stream after each kernel it
+ * enqueues.  ntt_profile_end() stops recording, waits for the last event
+ * and reports, for each kernel launched since begin (at most max_kernels),
+ * its device time in ms and its static name; *count gets the number of
+ * kernels.  Process-wide; not for concurrent use from several threads. */
+int ntt_profile_begin(void);
+int ntt_profile_end(int max_kernels, float* ms_out, const char** names_out, int* count);
+
+/* Integer-pipe throughput probe: `blocks` x `threads` threads run
+ * independent chains of 32-bit multiply-adds (kind 0) or of adds/xors
+ * (kind 1), 64 * iters operations each; writes operations per second to
+ * *ops_per_s (timed with CUDA events on `stream`; synchronous).  Allocates
+ * a small device buffer. */
+int ntt_int_probe(unsigned kind, int blocks, int threads, int iters, void* stream,
+                  double* ops_per_s);
+
+const char* ntt_status_str(int status);
+/* Details of the last error on the calling thread ("" if none). */
+const char* ntt_last_error(void);
+/* Library version string. */
+const char* ntt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBNTT_H */

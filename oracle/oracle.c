@@ -223,10 +223,15 @@ void orc_polymul(uint64_t p, const uint64_t* a, size_t na,
  * OpenMP threads when the library is built with OpenMP. */
 void orc_polymul_batch(uint64_t p, const uint64_t* a, size_t na,
                        const uint64_t* b, size_t nb, size_t count, uint64_t* c) {
-    long long t;
-#pragma omp parallel for schedule(dynamic, 1)
-    for (t = 0; t < (long long)count; t++)
-        orc_polymul(p, a + (size_t)t * na, na, b + (size_t)t * nb, nb, c + (size_t)t * (na + nb - 1));
+    if (na == 0 || nb == 0) return;
+    const size_t nc = na + nb - 1;
+    long long idx;
+    /* one work item per output coefficient of every product */
+#pragma omp parallel for schedule(dynamic, 256)
+    for (idx = 0; idx < (long long)(count * nc); idx++) {
+        const size_t t = (size_t)idx / nc, k = (size_t)idx % nc;
+        c[idx] = orc_poly_coeff(p, a + t * na, na, b + t * nb, nb, k);
+    }
 }
 
 /* Products of uneven shapes and moduli: product t has modulus ps[t],

@@ -1,0 +1,262 @@
+"""GB300 (sm_103a) exact modular NTT library: Python binding of libgbntt.so.
+
+Argument marshalling only: every step of every transform and product runs in
+the library's CUDA kernels.  Device buffers are torch tensors (uint32 words
+for p < 2^32, uint64 words for 2^32 <= p < 2^62); streams are torch CUDA
+streams.  The binding never computes a result itself and never falls back to
+another implementation: if the shared library is missing, every call raises.
+
+The calls and their semantics are those declared in include/gbntt.h, after
+van der Hoeven, Lecerf and Quintin, "Modular SIMD arithmetic in Mathemagix"
+(2014): the transform of Section 5.1, the polynomial product of Section 5.2
+and the modular products of Sections 2-3.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+LIB_PATH = os.path.join(HERE, "_build", "libgbntt.so")
+HEADER = os.path.join(ROOT, "include", "gbntt.h")
+
+NTT_OK = 0
+NTT_FLAG_PLAIN = 0x1
+NTT_FLAG_CHECK = 0x2
+NTT_SCHED_FUSED = 0
+NTT_SCHED_PLAIN = 1
+NTT_MM_BARRETT = 0
+NTT_MM_SHOUP = 1
+NTT_MM_MONTGOMERY = 2
+NTT_MM_FMA = 3
+NTT_MM_MONT_FIXED = 4
+NTT_MM_MONT_PRODUCT = 5
+
+_lock = threading.Lock()
+_lib = None
+
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+_sz = ctypes.c_size_t
+_vp = ctypes.c_void_p
+_int = ctypes.c_int
+_uint = ctypes.c_uint
+
+
+class NttError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = _load()
+        name = lib.ntt_status_str(status).decode()
+        detail = lib.ntt_last_error().decode()
+        super().__init__(f"{where}: {name} ({status}) {detail}")
+        self.status = status
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("p", _u64), ("g", _u64), ("omega", _u64), ("omega_inv", _u64),
+                ("n_inv", _u64), ("log2n", _u32), ("word_bytes", _u32), ("v2", _u32),
+                ("tile_max_log", _u32)]
+
+
+def header_functions() -> list[str]:
+    """Names of every function include/gbntt.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return re.findall(r"^[A-Za-z_][\w\s\*]*?\b(\w+)\s*\(", text, flags=re.M)
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgbntt.so is not built ({LIB_PATH}); "
+                               "run `python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "ntt_find_prime": (_int, [_uint, _uint, _uint, ctypes.POINTER(_u64)]),
+            "ntt_root_of_unity": (_int, [_u64, _uint, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+            "ntt_fixed_companion": (_int, [_u64, _uint, _uint, _vp, _vp, _sz]),
+            "ntt_plan_create": (_int, [_u64, _uint, _uint, ctypes.POINTER(_vp)]),
+            "ntt_plan_destroy": (_int, [_vp]),
+            "ntt_plan_get_info": (_int, [_vp, ctypes.POINTER(PlanInfo)]),
+            "ntt_forward": (_int, [_vp, _vp, _sz, _vp]),
+            "ntt_inverse": (_int, [_vp, _vp, _sz, _vp]),
+            "polymul_workspace_size": (_sz, [_vp, _sz, _uint]),
+            "polymul_mod_p_batch": (_int, [_vp, _vp, _sz, _vp, _sz, _sz, _vp, _uint, _vp, _sz, _vp]),
+            "polymul_mod_p": (_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp]),
+            "ntt_modmul_vec": (_int, [_u64, _uint, _uint, _vp, _vp, _vp, _vp, _sz, _vp]),
+            "ntt_status_str": (ctypes.c_char_p, [_int]),
+            "ntt_last_error": (ctypes.c_char_p, []),
+            "ntt_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def lib():
+    return _load()
+
+
+def _check(status: int, where: str):
+    if status != NTT_OK:
+        raise NttError(status, where)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------- host planning
+
+def ntt_find_prime(bits: int, min_l: int, index: int) -> int:
+    out = _u64()
+    _check(_load().ntt_find_prime(bits, min_l, index, ctypes.byref(out)), "ntt_find_prime")
+    return out.value
+
+
+def ntt_root_of_unity(p: int, log2n: int) -> tuple[int, int]:
+    g, w = _u64(), _u64()
+    _check(_load().ntt_root_of_unity(p, log2n, ctypes.byref(g), ctypes.byref(w)), "ntt_root_of_unity")
+    return g.value, w.value
+
+
+def ntt_fixed_companion(p: int, kind: int, word_bytes: int, y):
+    """Host companions (numpy uint64 in, numpy uint64 out)."""
+    import numpy as np
+    y = np.ascontiguousarray(np.asarray(y, dtype=np.uint64))
+    out = np.empty_like(y)
+    _check(_load().ntt_fixed_companion(p, kind, word_bytes, y.ctypes.data, out.ctypes.data,
+                                       y.size), "ntt_fixed_companion")
+    return out
+
+
+# ---------------------------------------------------------------- plans
+
+class Plan:
+    """An ntt_plan: modulus p, transform length 2^log2n, device tables."""
+
+    def __init__(self, p: int, log2n: int, flags: int = 0):
+        h = _vp()
+        _check(_load().ntt_plan_create(p, log2n, flags, ctypes.byref(h)), "ntt_plan_create")
+        self.handle = h.value
+        info = PlanInfo()
+        _check(_load().ntt_plan_get_info(self.handle, ctypes.byref(info)), "ntt_plan_get_info")
+        self.info = info
+        self.p = info.p
+        self.log2n = info.log2n
+        self.n = 1 << info.log2n
+        self.word_bytes = info.word_bytes
+        self.omega = info.omega
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.uint32 if self.word_bytes == 4 else torch.uint64
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _load().ntt_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def ntt_plan_create(p: int, log2n: int, flags: int = 0) -> Plan:
+    return Plan(p, log2n, flags)
+
+
+def ntt_forward(plan: Plan, data, batch: int | None = None, stream=None):
+    batch = data.numel() // plan.n if batch is None else batch
+    _check(_load().ntt_forward(plan.handle, _ptr(data), batch, _stream(stream)), "ntt_forward")
+
+
+def ntt_inverse(plan: Plan, data, batch: int | None = None, stream=None):
+    batch = data.numel() // plan.n if batch is None else batch
+    _check(_load().ntt_inverse(plan.handle, _ptr(data), batch, _stream(stream)), "ntt_inverse")
+
+
+def polymul_workspace_size(plan: Plan, batch: int, schedule: int = NTT_SCHED_FUSED) -> int:
+    return int(_load().polymul_workspace_size(plan.handle, batch, schedule))
+
+
+def polymul_mod_p_batch(plan: Plan, a, na: int, b, nb: int, batch: int, c,
+                        schedule: int = NTT_SCHED_FUSED, ws=None, ws_bytes: int | None = None,
+                        stream=None):
+    if ws_bytes is None:
+        ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    _check(_load().polymul_mod_p_batch(plan.handle, _ptr(a), na, _ptr(b), nb, batch, _ptr(c),
+                                       schedule, _ptr(ws), ws_bytes, _stream(stream)),
+           "polymul_mod_p_batch")
+
+
+def polymul_mod_p(plan: Plan, a, na: int, b, nb: int, c, ws=None, ws_bytes: int | None = None,
+                  stream=None):
+    if ws_bytes is None:
+        ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    _check(_load().polymul_mod_p(plan.handle, _ptr(a), na, _ptr(b), nb, _ptr(c), _ptr(ws),
+                                 ws_bytes, _stream(stream)), "polymul_mod_p")
+
+
+def ntt_modmul_vec(p: int, kind: int, word_bytes: int, x, y, yc, z, n: int | None = None,
+                   stream=None):
+    n = x.numel() if n is None else n
+    _check(_load().ntt_modmul_vec(p, kind, word_bytes, _ptr(x), _ptr(y), _ptr(yc), _ptr(z), n,
+                                  _stream(stream)), "ntt_modmul_vec")
+
+
+# ---------------------------------------------------------------- conveniences
+
+def alloc_workspace(plan: Plan, batch: int, schedule: int = NTT_SCHED_FUSED, device="cuda"):
+    """A uint8 device tensor of polymul_workspace_size bytes (None if 0)."""
+    import torch
+    nbytes = polymul_workspace_size(plan, batch, schedule)
+    if nbytes == 0:
+        return None
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def polymul_mod_p_batch_host(plan: Plan, h_a, na: int, h_b, nb: int, batch: int, h_c,
+                             d_a, d_b, d_c, ws=None, stream=None):
+    """polymul_mod_p_batch on host operands: copy a, b (pinned host tensors)
+    to the device staging buffers d_a, d_b, run the product into d_c and copy
+    it back to h_c, all enqueued on `stream` (asynchronous)."""
+    import torch
+    st = torch.cuda.current_stream() if stream is None else stream
+    with torch.cuda.stream(st):
+        d_a[: batch * na].copy_(h_a[: batch * na], non_blocking=True)
+        d_b[: batch * nb].copy_(h_b[: batch * nb], non_blocking=True)
+        polymul_mod_p_batch(plan, d_a, na, d_b, nb, batch, d_c, NTT_SCHED_FUSED, ws, stream=st)
+        nc = batch * (na + nb - 1)
+        h_c[:nc].copy_(d_c[:nc], non_blocking=True)

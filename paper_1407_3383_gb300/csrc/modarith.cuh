@@ -1,0 +1,104 @@
+// Device modular arithmetic for the NTT kernels (sm_103a).
+//
+// Residues live in {0, ..., p-1} at every kernel boundary (Section 2: modular
+// integers are stored as their representative in that range).  Two word
+// policies drive every transform kernel:
+//
+//  * Mont32 -- odd p < 2^32 in 32-bit words, including the full-word case
+//    m = n = 32 (p = 3*2^30+1).  Products by a fixed multiplicand (the
+//    twiddles) use Montgomery's reduction with the precomputed multiplicand
+//    of Remark 8 (Section 2.3.1): with w~ = w 2^32 rem p and
+//    phi = w~ p^-1 rem 2^32, the product x w rem p is
+//    hi(x w~) - hi((x phi rem 2^32) p), corrected once by +p.  The low halves
+//    of x w~ and of the quotient times p agree by construction, so this is
+//    the exact (x w~ - q p) / 2^32 of Function 13 written with the
+//    subtracted quotient instead of the added one; it needs no overflow test
+//    even when m = n and accepts any 32-bit x.  The general product (the
+//    pointwise step) is Function 13 on the full product x y, giving
+//    x y 2^-32 rem p; the 2^32 is folded into the final scaling.
+//    Addition is Function 4's max/compare form (valid for m = n), written
+//    with one compare: x + y rem p = x - (p - y), plus p when x < p - y.
+//
+//  * Shoup64 -- p < 2^62 in 64-bit words.  Fixed-multiplicand products use
+//    Function 8 with n = 64 and psi = floor(2^64 w / p) (Proposition 4: the
+//    quotient estimate is at most one short, so one conditional subtraction
+//    finishes); since m <= n - 1 the difference fits in one word (the remark
+//    after Proposition 4).  General products use Montgomery's reduction with
+//    m = n = 64 as in the 32-bit case.  Additions use Function 1's
+//    compare-and-subtract (no overflow since m <= n - 1).
+#pragma once
+#include <cstdint>
+
+namespace gbntt {
+
+struct Tw32 { uint32_t w, c; };   // twiddle in Montgomery form + companion
+struct Tw64 { uint64_t w, c; };   // twiddle + Shoup quotient
+
+struct Mont32 {
+    using word = uint32_t;
+    using tw = Tw32;
+    static constexpr int kBits = 32;
+    uint32_t p;      // odd modulus < 2^32
+    uint32_t pinv;   // p^-1 rem 2^32
+
+    __device__ __forceinline__ uint32_t add(uint32_t x, uint32_t y) const {
+        uint32_t a = p - y;            // in (0, p]
+        uint32_t d = x - a;            // x + y - p (mod 2^32)
+        return (x >= a) ? d : d + p;
+    }
+    __device__ __forceinline__ uint32_t sub(uint32_t x, uint32_t y) const {
+        uint32_t d = x - y;
+        return (x >= y) ? d : d + p;
+    }
+    // x * w rem p for any 32-bit x; t = (w 2^32 rem p, (w 2^32 rem p) p^-1 rem 2^32).
+    __device__ __forceinline__ uint32_t mulw(uint32_t x, Tw32 t) const {
+        uint32_t q = x * t.c;
+        uint32_t h = __umulhi(x, t.w);
+        uint32_t l = __umulhi(q, p);
+        uint32_t r = h - l;
+        return (h >= l) ? r : r + p;
+    }
+    // x * y * 2^-32 rem p for x, y < p.
+    __device__ __forceinline__ uint32_t mulmont(uint32_t x, uint32_t y) const {
+        uint32_t lo = x * y;
+        uint32_t hi = __umulhi(x, y);
+        uint32_t q = lo * pinv;
+        uint32_t l = __umulhi(q, p);
+        uint32_t r = hi - l;
+        return (hi >= l) ? r : r + p;
+    }
+};
+
+struct Shoup64 {
+    using word = uint64_t;
+    using tw = Tw64;
+    static constexpr int kBits = 64;
+    uint64_t p;      // modulus < 2^62
+    uint64_t pinv;   // p^-1 rem 2^64
+
+    __device__ __forceinline__ uint64_t add(uint64_t x, uint64_t y) const {
+        uint64_t s = x + y;
+        return (s >= p) ? s - p : s;
+    }
+    __device__ __forceinline__ uint64_t sub(uint64_t x, uint64_t y) const {
+        uint64_t d = x - y;
+        return (x >= y) ? d : d + p;
+    }
+    // x * w rem p for any 64-bit x; t = (w, floor(2^64 w / p)).
+    __device__ __forceinline__ uint64_t mulw(uint64_t x, Tw64 t) const {
+        uint64_t c = __umul64hi(x, t.c);
+        uint64_t r = x * t.w - c * p;      // in [0, 2p) < 2^63
+        return (r >= p) ? r - p : r;
+    }
+    // x * y * 2^-64 rem p for x, y < p.
+    __device__ __forceinline__ uint64_t mulmont(uint64_t x, uint64_t y) const {
+        uint64_t lo = x * y;
+        uint64_t hi = __umul64hi(x, y);
+        uint64_t q = lo * pinv;
+        uint64_t l = __umul64hi(q, p);
+        uint64_t r = hi - l;
+        return (hi >= l) ? r : r + p;
+    }
+};
+
+}  // namespace gbntt

@@ -1,0 +1,535 @@
+// Transform and polynomial-product kernels (sm_103a) and their launchers.
+//
+// Fused schedule (the library's default):
+//   n <= 2^tile_max_log : one thread block per product (several for short
+//       vectors); load with zero padding, two forward transforms, pointwise
+//       product, inverse transform and scaled store, all in shared memory.
+//   larger n : Algorithm 1 once more at the global level, n = n2 x n1
+//       (n2 = 2^floor(k/2) rows of n1 words):
+//       pass 1  columns: load (zero padded) n2 x w slabs, transform each
+//               column, apply the step-2 twiddle w_n^(j1 [j2]), write;
+//       pass 2  rows: transform rows of both operands, multiply them
+//               pointwise, inverse-transform the product rows, write;
+//       pass 3  columns: inverse twiddle, inverse column transforms, scale
+//               by n^-1 (and the Montgomery factor), crop, store.
+//   Operand traffic: read a, b once; write c once; the transformed operands
+//   make one round trip through the caller's workspace.
+//
+// Plain schedule (the baseline the fused one is measured against): one
+// launch per radix-2 stage over global memory.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+
+#include "../../include/gbntt.h"
+#include "kernels.h"
+#include "plan.h"
+
+namespace gbntt {
+
+constexpr int kThreads = 256;
+
+__host__ __device__ inline VecLayout tile_layout(int logL, int lognvec) {
+    VecLayout L{};
+    L.logL = logL;
+    L.lognvec = lognvec;
+    if (logL <= kMaxLineLog) {
+        L.CS = 1;
+        L.RS = 0;
+        L.VS = (1LL << logL) + 1;
+        L.vfast = true;
+    } else {
+        const long long L1 = 1LL << tile_l1(logL), L2 = 1LL << tile_l2(logL);
+        L.CS = 1;
+        L.RS = L1 + 1;
+        L.VS = L2 * L.RS;
+        L.vfast = false;
+    }
+    return L;
+}
+
+__host__ __device__ inline long long layout_words(const VecLayout& L) {
+    return (1LL << L.lognvec) * L.VS;
+}
+
+// w columns (vectors) of length 2^logL, element i of column v at v + i*(w+1)
+// (with one extra word per tile row when the column is itself a tile).
+__host__ __device__ inline VecLayout slab_layout(int logL, int logw) {
+    VecLayout L{};
+    const long long w = 1LL << logw;
+    L.logL = logL;
+    L.lognvec = logw;
+    L.VS = 1;
+    L.CS = w + 1;
+    L.vfast = true;
+    if (logL > kMaxLineLog) L.RS = (1LL << tile_l1(logL)) * (w + 1) + 1;
+    return L;
+}
+
+__host__ __device__ inline long long slab_words(const VecLayout& L) {
+    if (L.logL <= kMaxLineLog) return (1LL << L.logL) * L.CS;
+    return (1LL << tile_l2(L.logL)) * L.RS;
+}
+
+// ------------------------------------------------------------------ fused kernels
+
+template <class Ar>
+__global__ void __launch_bounds__(kThreads)
+k_tile_polymul(DevPlan<Ar> P, const typename Ar::word* __restrict__ a, long long na,
+               const typename Ar::word* __restrict__ b, long long nb,
+               typename Ar::word* __restrict__ c, long long batch, int logL, int lppc,
+               typename Ar::tw scale) {
+    using word = typename Ar::word;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    word* sm = reinterpret_cast<word*>(smraw);
+    const int ppc = 1 << lppc;
+    const long long prod0 = static_cast<long long>(blockIdx.x) << lppc;
+    const long long L = 1LL << logL;
+    const VecLayout LA = tile_layout(logL, lppc + 1);
+    for (long long idx = threadIdx.x; idx < (L << lppc); idx += blockDim.x) {
+        const int v = static_cast<int>(idx >> logL);
+        const long long i = idx & (L - 1);
+        const long long prod = prod0 + v;
+        word xa = 0, xb = 0;
+        if (prod < batch) {
+            if (i < na) xa = a[prod * na + i];
+            if (i < nb) xb = b[prod * nb + i];
+        }
+        sm[vec_addr(LA, v, i)] = xa;
+        sm[vec_addr(LA, v + ppc, i)] = xb;
+    }
+    __syncthreads();
+    vec_fwd<Ar>(P, sm, LA, nullptr);
+    for (long long idx = threadIdx.x; idx < (L << lppc); idx += blockDim.x) {
+        const int v = static_cast<int>(idx >> logL);
+        const long long i = idx & (L - 1);
+        const long long pa = vec_addr(LA, v, i), pb = vec_addr(LA, v + ppc, i);
+        sm[pa] = P.ar.mulmont(sm[pa], sm[pb]);
+    }
+    __syncthreads();
+    const VecLayout LC = tile_layout(logL, lppc);
+    vec_inv<Ar>(P, sm, LC, nullptr);
+    const long long nc = na + nb - 1;
+    for (long long idx = threadIdx.x; idx < (nc << lppc); idx += blockDim.x) {
+        const int v = static_cast<int>(idx / nc);
+        const long long i = idx - v * nc;
+        const long long prod = prod0 + v;
+        if (prod < batch) c[prod * nc + i] = P.ar.mulw(sm[vec_addr(LC, v, i)], scale);
+    }
+}
+
+template <class Ar, bool FWD>
+__global__ void __launch_bounds__(kThreads)
+k_tile_ntt(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long batch, int logL,
+           int lppc, typename Ar::tw scale) {
+    using word = typename Ar::word;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    word* sm = reinterpret_cast<word*>(smraw);
+    const long long prod0 = static_cast<long long>(blockIdx.x) << lppc;
+    const long long L = 1LL << logL;
+    const VecLayout LA = tile_layout(logL, lppc);
+    for (long long idx = threadIdx.x; idx < (L << lppc); idx += blockDim.x) {
+        const int v = static_cast<int>(idx >> logL);
+        const long long i = idx & (L - 1);
+        const long long prod = prod0 + v;
+        sm[vec_addr(LA, v, i)] = (prod < batch) ? data[prod * L + i] : word(0);
+    }
+    __syncthreads();
+    if (FWD)
+        vec_fwd<Ar>(P, sm, LA, nullptr);
+    else
+        vec_inv<Ar>(P, sm, LA, nullptr);
+    for (long long idx = threadIdx.x; idx < (L << lppc); idx += blockDim.x) {
+        const int v = static_cast<int>(idx >> logL);
+        const long long i = idx & (L - 1);
+        const long long prod = prod0 + v;
+        if (prod < batch) {
+            word x = sm[vec_addr(LA, v, i)];
+            data[prod * L + i] = FWD ? x : P.ar.mulw(x, scale);
+        }
+    }
+}
+
+// Pass 1: forward column transforms of a slab of w columns, then the
+// global twiddle.  blockIdx.z selects operand 0 or 1 (src0/src1).
+template <class Ar>
+__global__ void __launch_bounds__(kThreads)
+k_col_fwd(DevPlan<Ar> P, const typename Ar::word* src0, long long len0,
+          const typename Ar::word* src1, long long len1, typename Ar::word* dst,
+          long long dst_stride, long long dst_off1, int logN, int k2, int logw, long long prod_base) {
+    using word = typename Ar::word;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    word* sm = reinterpret_cast<word*>(smraw);
+    const int k1 = logN - k2;
+    const long long n1 = 1LL << k1;
+    const int w = 1 << logw;
+    const long long c0 = static_cast<long long>(blockIdx.x) << logw;
+    const long long prod = prod_base + blockIdx.y;
+    const word* src = blockIdx.z ? src1 : src0;
+    const long long len = blockIdx.z ? len1 : len0;
+    word* out = dst + prod * dst_stride + (blockIdx.z ? dst_off1 : 0);
+    const VecLayout L = slab_layout(k2, logw);
+    const long long total = (1LL << k2) << logw;
+    for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const long long row = idx >> logw;
+        const int col = static_cast<int>(idx & (w - 1));
+        const long long e = row * n1 + c0 + col;
+        sm[vec_addr(L, col, row)] = (e < len) ? src[prod * len + e] : word(0);
+    }
+    __syncthreads();
+    Hook<Ar> h{P.glob_fwd, n1, 0, 1, c0};
+    vec_fwd<Ar>(P, sm, L, &h);
+    for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const long long row = idx >> logw;
+        const int col = static_cast<int>(idx & (w - 1));
+        out[row * n1 + c0 + col] = sm[vec_addr(L, col, row)];
+    }
+}
+
+// Pass 3: inverse twiddle and inverse column transforms, scaled, cropped
+// store of the first out_len words of each product.
+template <class Ar>
+__global__ void __launch_bounds__(kThreads)
+k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
+          typename Ar::word* dst, long long out_len, int logN, int k2, int logw,
+          typename Ar::tw scale, long long prod_base) {
+    using word = typename Ar::word;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    word* sm = reinterpret_cast<word*>(smraw);
+    const int k1 = logN - k2;
+    const long long n1 = 1LL << k1;
+    const int w = 1 << logw;
+    const long long c0 = static_cast<long long>(blockIdx.x) << logw;
+    const long long prod = prod_base + blockIdx.y;
+    const word* in = src + prod * src_stride;
+    const VecLayout L = slab_layout(k2, logw);
+    const long long total = (1LL << k2) << logw;
+    for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const long long row = idx >> logw;
+        const int col = static_cast<int>(idx & (w - 1));
+        sm[vec_addr(L, col, row)] = in[row * n1 + c0 + col];
+    }
+    __syncthreads();
+    Hook<Ar> h{P.glob_inv, n1, 0, 1, c0};
+    vec_inv<Ar>(P, sm, L, &h);
+    for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const long long row = idx >> logw;
+        const int col = static_cast<int>(idx & (w - 1));
+        const long long e = row * n1 + c0 + col;
+        if (e < out_len) dst[prod * out_len + e] = P.ar.mulw(sm[vec_addr(L, col, row)], scale);
+    }
+}
+
+// Pass 2 of the product: rows of both transformed operands -> forward row
+// transforms, pointwise product, inverse row transforms of the product.
+// ws per product: [0, n) operand a, [n, 2n) operand b; result over a.
+template <class Ar>
+__global__ void __launch_bounds__(kThreads)
+k_row_polymul(DevPlan<Ar> P, typename Ar::word* ws, long long ws_stride, int logN, int k2,
+              int lrpc, long long prod_base) {
+    using word = typename Ar::word;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    word* sm = reinterpret_cast<word*>(smraw);
+    const int k1 = logN - k2;
+    const long long n1 = 1LL << k1, N = 1LL << logN;
+    const int rpc = 1 << lrpc;
+    const long long r0 = static_cast<long long>(blockIdx.x) << lrpc;
+    word* base = ws + (prod_base + blockIdx.y) * ws_stride;
+    const VecLayout L = tile_layout(k1, lrpc + 1);
+    const long long total = (2LL << lrpc) << k1;
+    for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int v = static_cast<int>(idx >> k1);
+        const long long i = idx & (n1 - 1);
+        const int arr = v >> lrpc;
+        const long long row = r0 + (v & (rpc - 1));
+        sm[vec_addr(L, v, i)] = base[arr * N + row * n1 + i];
+    }
+    __syncthreads();
+    vec_fwd<Ar>(P, sm, L, nullptr);
+    for (long long idx = threadIdx.x; idx < (static_cast<long long>(rpc) << k1); idx += blockDim.x) {
+        const int v = static_cast<int>(idx >> k1);
+        const long long i = idx & (n1 - 1);
+        const long long pa = vec_addr(L, v, i), pb = vec_addr(L, v + rpc, i);
+        sm[pa] = P.ar.mulmont(sm[pa], sm[pb]);
+    }
+    __syncthreads();
+    const VecLayout LC = tile_layout(k1, lrpc);
+    vec_inv<Ar>(P, sm, LC, nullptr);
+    for (long long idx = threadIdx.x; idx < (static_cast<long long>(rpc) << k1); idx += blockDim.x) {
+        const int v = static_cast<int>(idx >> k1);
+        const long long i = idx & (n1 - 1);
+        base[(r0 + v) * n1 + i] = sm[vec_addr(LC, v, i)];
+    }
+}
+
+// Row transforms in place (standalone large transforms).
+template <class Ar, bool FWD>
+__global__ void __launch_bounds__(kThreads)
+k_row_ntt(DevPlan<Ar> P, typename Ar::word* data, int logN, int k2, int lrpc, long long prod_base) {
+    using word = typename Ar::word;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    word* sm = reinterpret_cast<word*>(smraw);
+    const int k1 = logN - k2;
+    const long long n1 = 1LL << k1;
+    const long long r0 = static_cast<long long>(blockIdx.x) << lrpc;
+    word* base = data + ((prod_base + blockIdx.y) << logN);
+    const VecLayout L = tile_layout(k1, lrpc);
+    const long long total = (1LL << lrpc) << k1;
+    for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int v = static_cast<int>(idx >> k1);
+        const long long i = idx & (n1 - 1);
+        sm[vec_addr(L, v, i)] = base[(r0 + v) * n1 + i];
+    }
+    __syncthreads();
+    if (FWD)
+        vec_fwd<Ar>(P, sm, L, nullptr);
+    else
+        vec_inv<Ar>(P, sm, L, nullptr);
+    for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int v = static_cast<int>(idx >> k1);
+        const long long i = idx & (n1 - 1);
+        base[(r0 + v) * n1 + i] = sm[vec_addr(L, v, i)];
+    }
+}
+
+// ------------------------------------------------------------------ plain kernels
+
+template <class Ar>
+__global__ void k_plain_load(const typename Ar::word* a, long long na, const typename Ar::word* b,
+                             long long nb, typename Ar::word* ws, int logN, long long batch) {
+    const long long N = 1LL << logN;
+    const long long total = (2 * batch) << logN;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long arr = idx >> logN, i = idx & (N - 1);
+        typename Ar::word x = 0;
+        if (arr < batch) {
+            if (i < na) x = a[arr * na + i];
+        } else if (i < nb) {
+            x = b[(arr - batch) * nb + i];
+        }
+        ws[idx] = x;
+    }
+}
+
+// One radix-2 DIF stage of half-span 2^logh on narr arrays of 2^logN words.
+template <class Ar>
+__global__ void k_plain_dif(DevPlan<Ar> P, typename Ar::word* ws, long long narr, int logN, int logh) {
+    const long long half = 1LL << (logN - 1);
+    const long long total = narr * half;
+    const long long h = 1LL << logh;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long arr = idx >> (logN - 1), i = idx & (half - 1);
+        const long long j = i & (h - 1), blk = i >> logh;
+        typename Ar::word* x = ws + (arr << logN) + (blk << (logh + 1)) + j;
+        const auto u = x[0], v = x[h];
+        x[0] = P.ar.add(u, v);
+        x[h] = P.ar.mulw(P.ar.sub(u, v), P.plain_fwd[j << (logN - 1 - logh)]);
+    }
+}
+
+template <class Ar>
+__global__ void k_plain_dit(DevPlan<Ar> P, typename Ar::word* ws, long long narr, int logN, int logh) {
+    const long long half = 1LL << (logN - 1);
+    const long long total = narr * half;
+    const long long h = 1LL << logh;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long arr = idx >> (logN - 1), i = idx & (half - 1);
+        const long long j = i & (h - 1), blk = i >> logh;
+        typename Ar::word* x = ws + (arr << logN) + (blk << (logh + 1)) + j;
+        const auto u = x[0];
+        const auto t = P.ar.mulw(x[h], P.plain_inv[j << (logN - 1 - logh)]);
+        x[0] = P.ar.add(u, t);
+        x[h] = P.ar.sub(u, t);
+    }
+}
+
+template <class Ar>
+__global__ void k_plain_pointwise(DevPlan<Ar> P, typename Ar::word* ws, long long count,
+                                  long long boff) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < count;
+         idx += (long long)gridDim.x * blockDim.x)
+        ws[idx] = P.ar.mulmont(ws[idx], ws[idx + boff]);
+}
+
+template <class Ar>
+__global__ void k_plain_store(DevPlan<Ar> P, const typename Ar::word* ws, typename Ar::word* c,
+                              long long nc, int logN, long long batch, typename Ar::tw scale) {
+    const long long total = batch * nc;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long arr = idx / nc, i = idx - arr * nc;
+        c[idx] = P.ar.mulw(ws[(arr << logN) + i], scale);
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+template <class K>
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(bytes));
+}
+
+static int grid_for(long long total) {
+    long long blocks = (total + kThreads - 1) / kThreads;
+    return static_cast<int>(std::max(1LL, std::min(blocks, 152LL * 32)));
+}
+
+template <class Ar>
+static int col_logw(int k2) {
+    using word = typename Ar::word;
+    int logw = (sizeof(word) == 4) ? 5 : 4;          // 128-byte row segments
+    const int min_logw = (sizeof(word) == 4) ? 3 : 2; // 32-byte sectors at least
+    while (logw > min_logw &&
+           slab_words(slab_layout(k2, logw)) * (long long)sizeof(word) > 100 * 1024)
+        --logw;
+    return logw;
+}
+
+static int row_lrpc(int k1, int operands) {
+    // short rows: enough rows that the lanes of a warp span >= 32 lines
+    if (k1 <= kMaxLineLog) return operands == 2 ? 4 : 5;
+    return operands == 2 ? 0 : 1;
+}
+
+static int check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        gbntt_set_error(std::string(what) + ": " + cudaGetErrorString(e));
+        return NTT_ERR_CUDA;
+    }
+    return NTT_OK;
+}
+
+static constexpr long long kMaxGridY = 65535;
+
+template <class Ar>
+int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
+                         long long na, const typename Ar::word* b, long long nb, long long batch,
+                         typename Ar::word* c, typename Ar::word* ws, typename Ar::tw scale,
+                         cudaStream_t st) {
+    using word = typename Ar::word;
+    const int k = static_cast<int>(plan->log2n);
+    prof_begin_call(st);
+    if (k <= plan->tile_max_log) {
+        const int lppc = (k <= kMaxLineLog) ? 4 : 0;
+        const size_t smem = layout_words(tile_layout(k, lppc + 1)) * sizeof(word);
+        if (allow_smem(k_tile_polymul<Ar>, smem) != cudaSuccess) return check_launch("smem attr");
+        const long long blocks = (batch + (1LL << lppc) - 1) >> lppc;
+        for (long long b0 = 0; b0 < blocks; b0 += 0x7fffffffLL) {
+            const long long nb0 = std::min(blocks - b0, 0x7fffffffLL);
+            const long long p0 = b0 << lppc;
+            k_tile_polymul<Ar><<<static_cast<unsigned>(nb0), kThreads, smem, st>>>(
+                dp, a + p0 * na, na, b + p0 * nb, nb, c + p0 * (na + nb - 1), batch - p0, k, lppc,
+                scale);
+            prof_mark(st, "k_tile_polymul");
+        }
+        return check_launch("k_tile_polymul");
+    }
+    const int k2 = plan->k2, k1 = plan->k1;
+    const long long N = 1LL << k;
+    const int logw = col_logw<Ar>(k2);
+    const size_t smem_c = slab_words(slab_layout(k2, logw)) * sizeof(word);
+    const int lrpc = row_lrpc(k1, 2);
+    const size_t smem_r = layout_words(tile_layout(k1, lrpc + 1)) * sizeof(word);
+    if (allow_smem(k_col_fwd<Ar>, smem_c) != cudaSuccess ||
+        allow_smem(k_col_inv<Ar>, smem_c) != cudaSuccess ||
+        allow_smem(k_row_polymul<Ar>, smem_r) != cudaSuccess)
+        return check_launch("smem attr");
+    for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
+        const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
+        dim3 gc(static_cast<unsigned>((1LL << k1) >> logw), nbat, 2);
+        k_col_fwd<Ar><<<gc, kThreads, smem_c, st>>>(dp, a, na, b, nb, ws, 2 * N, N, k, k2, logw, p0);
+        prof_mark(st, "k_col_fwd");
+        dim3 gr(static_cast<unsigned>((1LL << k2) >> lrpc), nbat, 1);
+        k_row_polymul<Ar><<<gr, kThreads, smem_r, st>>>(dp, ws, 2 * N, k, k2, lrpc, p0);
+        prof_mark(st, "k_row_polymul");
+        dim3 gi(static_cast<unsigned>((1LL << k1) >> logw), nbat, 1);
+        k_col_inv<Ar><<<gi, kThreads, smem_c, st>>>(dp, ws, 2 * N, c, na + nb - 1, k, k2, logw,
+                                                    scale, p0);
+        prof_mark(st, "k_col_inv");
+    }
+    return check_launch("fused polymul passes");
+}
+
+template <class Ar>
+int launch_polymul_plain(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
+                         long long na, const typename Ar::word* b, long long nb, long long batch,
+                         typename Ar::word* c, typename Ar::word* ws, typename Ar::tw scale,
+                         cudaStream_t st) {
+    const int k = static_cast<int>(plan->log2n);
+    const long long N = 1LL << k;
+    prof_begin_call(st);
+    k_plain_load<Ar><<<grid_for(2 * batch * N), kThreads, 0, st>>>(a, na, b, nb, ws, k, batch);
+    prof_mark(st, "k_plain_load");
+    for (int lh = k - 1; lh >= 0; --lh) {
+        k_plain_dif<Ar><<<grid_for(batch * N), kThreads, 0, st>>>(dp, ws, 2 * batch, k, lh);
+        prof_mark(st, "k_plain_dif");
+    }
+    k_plain_pointwise<Ar><<<grid_for(batch * N), kThreads, 0, st>>>(dp, ws, batch * N, batch * N);
+    prof_mark(st, "k_plain_pointwise");
+    for (int lh = 0; lh < k; ++lh) {
+        k_plain_dit<Ar><<<grid_for(batch * N / 2), kThreads, 0, st>>>(dp, ws, batch, k, lh);
+        prof_mark(st, "k_plain_dit");
+    }
+    k_plain_store<Ar><<<grid_for(batch * (na + nb - 1)), kThreads, 0, st>>>(dp, ws, c, na + nb - 1,
+                                                                           k, batch, scale);
+    prof_mark(st, "k_plain_store");
+    return check_launch("plain polymul stages");
+}
+
+template <class Ar>
+int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* data, long long batch,
+               bool fwd, typename Ar::tw scale, cudaStream_t st) {
+    using word = typename Ar::word;
+    const int k = static_cast<int>(plan->log2n);
+    if (k <= plan->tile_max_log) {
+        const int lppc = (k <= kMaxLineLog) ? 5 : 0;
+        const size_t smem = layout_words(tile_layout(k, lppc)) * sizeof(word);
+        auto kern = fwd ? k_tile_ntt<Ar, true> : k_tile_ntt<Ar, false>;
+        if (allow_smem(kern, smem) != cudaSuccess) return check_launch("smem attr");
+        const long long blocks = (batch + (1LL << lppc) - 1) >> lppc;
+        prof_begin_call(st);
+        kern<<<static_cast<unsigned>(blocks), kThreads, smem, st>>>(dp, data, batch, k, lppc, scale);
+        prof_mark(st, fwd ? "k_tile_ntt_fwd" : "k_tile_ntt_inv");
+        return check_launch("k_tile_ntt");
+    }
+    const int k2 = plan->k2, k1 = plan->k1;
+    const long long N = 1LL << k;
+    const int logw = col_logw<Ar>(k2);
+    const size_t smem_c = slab_words(slab_layout(k2, logw)) * sizeof(word);
+    const int lrpc = row_lrpc(k1, 1);
+    const size_t smem_r = layout_words(tile_layout(k1, lrpc)) * sizeof(word);
+    auto krow = fwd ? k_row_ntt<Ar, true> : k_row_ntt<Ar, false>;
+    if (allow_smem(k_col_fwd<Ar>, smem_c) != cudaSuccess ||
+        allow_smem(k_col_inv<Ar>, smem_c) != cudaSuccess || allow_smem(krow, smem_r) != cudaSuccess)
+        return check_launch("smem attr");
+    prof_begin_call(st);
+    for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
+        const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
+        dim3 gc(static_cast<unsigned>((1LL << k1) >> logw), nbat, 1);
+        dim3 gr(static_cast<unsigned>((1LL << k2) >> lrpc), nbat, 1);
+        if (fwd) {
+            k_col_fwd<Ar><<<gc, kThreads, smem_c, st>>>(dp, data, N, data, N, data, N, 0, k, k2,
+                                                        logw, p0);
+            prof_mark(st, "k_col_fwd");
+            krow<<<gr, kThreads, smem_r, st>>>(dp, data, k, k2, lrpc, p0);
+            prof_mark(st, "k_row_ntt_fwd");
+        } else {
+            krow<<<gr, kThreads, smem_r, st>>>(dp, data, k, k2, lrpc, p0);
+            prof_mark(st, "k_row_ntt_inv");
+            k_col_inv<Ar><<<gc, kThreads, smem_c, st>>>(dp, data, N, data, N, k, k2, logw, scale,
+                                                        p0);
+            prof_mark(st, "k_col_inv");
+        }
+    }
+    return check_launch("ntt passes");
+}
+
+}  // namespace gbntt

@@ -1,0 +1,15 @@
+// Transform and product kernels instantiated for 64-bit words (Shoup64).
+#include "ntt_kernels.cuh"
+
+namespace gbntt {
+
+template int launch_polymul_fused<Shoup64>(const ntt_plan*, const DevPlan<Shoup64>&, const uint64_t*,
+                                           long long, const uint64_t*, long long, long long,
+                                           uint64_t*, uint64_t*, Tw64, cudaStream_t);
+template int launch_polymul_plain<Shoup64>(const ntt_plan*, const DevPlan<Shoup64>&, const uint64_t*,
+                                           long long, const uint64_t*, long long, long long,
+                                           uint64_t*, uint64_t*, Tw64, cudaStream_t);
+template int launch_ntt<Shoup64>(const ntt_plan*, const DevPlan<Shoup64>&, uint64_t*, long long,
+                                 bool, Tw64, cudaStream_t);
+
+}  // namespace gbntt

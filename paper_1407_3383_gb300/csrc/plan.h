@@ -1,0 +1,48 @@
+// Internal plan object behind the opaque `ntt_plan` handle.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "engine.cuh"
+
+struct ntt_plan {
+    uint64_t p = 0;
+    unsigned log2n = 0;
+    unsigned flags = 0;
+    unsigned word_bytes = 0;    // 4 (p < 2^32) or 8 (p < 2^62)
+    unsigned v2 = 0;            // 2-adic valuation of p - 1
+    uint64_t g = 0;             // least generator of F_p^*
+    uint64_t omega = 0;         // g^((p-1)/n)
+    uint64_t omega_inv = 0;
+    uint64_t n_inv = 0;
+    int device = 0;
+    int tile_max_log = 0;       // largest n done by one CTA (both operands resident)
+    int k2 = 0, k1 = 0;         // n = 2^k2 rows x 2^k1 columns when log2n > tile_max_log
+    void* d_tables = nullptr;   // one device allocation holding every table
+    size_t table_bytes = 0;
+    gbntt::DevPlan<gbntt::Mont32> dp32{};
+    gbntt::DevPlan<gbntt::Shoup64> dp64{};
+    // scaling constants, already in the policy's multiplicand form
+    gbntt::Tw32 inv_scale32{}, pm_scale32{};   // n^-1 ; n^-1 * 2^32 (after Montgomery products)
+    gbntt::Tw64 inv_scale64{}, pm_scale64{};   // n^-1 ; n^-1 * 2^64
+};
+
+namespace gbntt {
+namespace host {
+
+uint64_t mul_mod(uint64_t a, uint64_t b, uint64_t p);
+uint64_t pow_mod(uint64_t a, uint64_t e, uint64_t p);
+bool is_prime_u64(uint64_t n);
+uint64_t least_generator(uint64_t p);
+unsigned two_adic(uint64_t x);
+uint32_t inv_pow2_32(uint32_t p);   // p^-1 rem 2^32 (p odd)
+uint64_t inv_pow2_64(uint64_t p);   // p^-1 rem 2^64 (p odd)
+Tw32 tw32_of(uint64_t value, uint32_t p, uint32_t pinv);
+Tw64 tw64_of(uint64_t value, uint64_t p);
+
+}  // namespace host
+}  // namespace gbntt
+
+// Thread-local last error message for ntt_last_error().
+void gbntt_set_error(const std::string& msg);

@@ -28,3 +28,12 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+def pytest_sessionstart(session):
+    # Compile the CUDA library and the oracle if a source is newer than the
+    # built file (no-op otherwise); both are needed by CPU and GPU tests.
+    from paper_1407_3383_gb300 import build as libbuild
+    import oracle
+    libbuild.build()
+    oracle.build()

@@ -1,0 +1,149 @@
+"""GPU parity of the polynomial product over Z/pZ (Section 5.2) with the
+oracle's schoolbook product, bit for bit.
+
+Full comparisons where the schoolbook oracle finishes in seconds (sizes that
+span several tiles and a ragged tail); at the full workload sizes, in the
+launch configuration the benchmark times, sampled coefficients (each one an
+O(L) oracle sum) plus evaluation fingerprints C(x) = A(x) B(x)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1407_3383_gb300 as G
+from paper_1407_3383_gb300 import workloads as W
+from helpers import empty_dev, from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _polymul(p, log2n, a, b, schedule=G.NTT_SCHED_FUSED, flags=0):
+    """a: (batch, na), b: (batch, nb) numpy -> (batch, na+nb-1) numpy."""
+    import torch
+    batch, na = a.shape
+    _, nb = b.shape
+    with G.Plan(p, log2n, flags) as plan:
+        wb = plan.word_bytes
+        da, db = to_dev(a.reshape(-1), wb), to_dev(b.reshape(-1), wb)
+        dc = empty_dev(batch * (na + nb - 1), wb)
+        ws = G.alloc_workspace(plan, batch, schedule)
+        G.polymul_mod_p_batch(plan, da, na, db, nb, batch, dc, schedule, ws)
+        torch.cuda.synchronize()
+        return from_dev(dc).reshape(batch, na + nb - 1)
+
+
+def test_config0_single_product_full():
+    """One product mod 998244353 of two length-2048 operands through a
+    size-4096 transform: all 4095 coefficients."""
+    p, a, b = W.config0()
+    got = _polymul(p, 12, a[None, :], b[None, :])
+    assert (got[0] == O.polymul(p, a, b)).all()
+
+
+@pytest.mark.parametrize("schedule", [G.NTT_SCHED_FUSED, G.NTT_SCHED_PLAIN])
+@pytest.mark.parametrize("p,log2n,na,nb,batch", [
+    (W.P_B, 5, 17, 16, 19),        # short vectors, many per block, ragged batch
+    (W.P_A, 8, 128, 129, 33),      # one-line vectors at the 256 limit
+    (W.P_B, 9, 300, 200, 5),       # first tiled size
+    (W.P_B, 14, 8192, 8192, 2),    # largest one-block tile (u32)
+    (W.P_B, 15, 9000, 7001, 2),    # two global passes, ragged lengths
+    (W.P_A, 16, 1 << 15, 1 << 15, 2),
+    (W.P1, 7, 64, 64, 21),
+    (W.P2, 13, 4096, 4096, 2),     # largest one-block tile (u64)
+    (W.P3, 14, 5000, 3000, 2),     # two global passes (u64)
+    (W.P1, 12, 1, 1, 3),           # degree-0 operands
+    (W.P_B, 6, 1, 40, 4),
+])
+def test_polymul_full(schedule, p, log2n, na, nb, batch):
+    if schedule == G.NTT_SCHED_PLAIN and log2n < 2:
+        pytest.skip()
+    g = W.SplitMix64(p + log2n * 1000 + na)
+    a = g.uniform_mod(p, batch * na).reshape(batch, na)
+    b = g.uniform_mod(p, batch * nb).reshape(batch, nb)
+    flags = G.NTT_FLAG_PLAIN if schedule == G.NTT_SCHED_PLAIN else 0
+    got = _polymul(p, log2n, a, b, schedule, flags)
+    want = O.polymul_batch(p, a, b)
+    assert (got == want).all()
+
+
+def test_extreme_residues():
+    """Operands all p - 1: c_k = (number of terms) (p-1)^2 = #terms (mod p)."""
+    for p, log2n, n in [(W.P_B, 16, 1 << 15), (W.P1, 14, 1 << 13), (W.P_A, 12, 2048)]:
+        a = np.full((1, n), p - 1, dtype=np.uint64)
+        got = _polymul(p, log2n, a, a)[0]
+        k = np.arange(2 * n - 1)
+        terms = np.minimum(k, n - 1) - np.maximum(0, k - n + 1) + 1
+        assert (got == terms.astype(np.uint64) % np.uint64(p)).all()
+
+
+def _sampled_check(p, a, b, got, samples, seed):
+    batch, na = a.shape
+    nb = b.shape[1]
+    g = W.SplitMix64(seed)
+    prods = (g.u64(samples) % np.uint64(batch)).astype(np.int64)
+    ks = (g.u64(samples) % np.uint64(na + nb - 1)).astype(np.int64)
+    prods = np.concatenate([prods, [0, batch - 1, batch - 1]])
+    ks = np.concatenate([ks, [0, na + nb - 2, (na + nb) // 2]])
+    for t, k in zip(prods, ks):
+        assert int(got[t, k]) == O.poly_coeff(p, a[t], b[t], int(k)), (t, k)
+    # fingerprints C(x) = A(x) B(x) at random points for several products
+    for t in sorted(set(prods[:8].tolist())):
+        for x in g.uniform_mod(p, 2):
+            x = int(x)
+            lhs = O.eval_poly(p, got[t], x)
+            rhs = O.mulmod(O.eval_poly(p, a[t], x), O.eval_poly(p, b[t], x), p)
+            assert lhs == rhs, (t, x)
+
+
+@pytest.mark.parametrize("schedule", [G.NTT_SCHED_FUSED, G.NTT_SCHED_PLAIN])
+def test_config1_full_size_sampled(schedule):
+    """256 products mod 3*2^30+1 of length-2^15 operands (size-2^16
+    transforms), exactly as the benchmark runs them."""
+    p, a, b = W.config1()
+    flags = G.NTT_FLAG_PLAIN if schedule == G.NTT_SCHED_PLAIN else 0
+    got = _polymul(p, 16, a, b, schedule, flags)
+    _sampled_check(p, a.astype(np.uint64), b.astype(np.uint64), got, 64, 11)
+    # a few products in full against the schoolbook oracle
+    idx = [0, 255]
+    want = O.polymul_batch(p, a[idx].astype(np.uint64), b[idx].astype(np.uint64))
+    assert (got[idx] == want).all()
+
+
+def test_config2_products_sampled():
+    """1024 products of length 2^12 mod the 62-bit prime (size-2^13 transforms)."""
+    p, a, b = W.config2_products()
+    got = _polymul(p, 13, a, b)
+    _sampled_check(p, a, b, got, 64, 12)
+    want = O.polymul_batch(p, a[:8], b[:8])
+    assert (got[:8] == want).all()
+
+
+def test_fused_equals_plain_bitwise():
+    p, a, b = W.config1(count=4)
+    f = _polymul(p, 16, a, b, G.NTT_SCHED_FUSED)
+    q = _polymul(p, 16, a, b, G.NTT_SCHED_PLAIN, G.NTT_FLAG_PLAIN)
+    assert (f == q).all()
+
+
+def test_errors_are_reported():
+    import torch
+    with G.Plan(W.P_A, 10) as plan:
+        a = torch.zeros(600, dtype=torch.uint32, device="cuda")
+        c = torch.zeros(2000, dtype=torch.uint32, device="cuda")
+        with pytest.raises(G.NttError) as e:
+            G.polymul_mod_p_batch(plan, a, 600, a, 600, 1, c)       # 1199 > 1024
+        assert e.value.status == 5
+        with pytest.raises(G.NttError) as e:
+            G.polymul_mod_p_batch(plan, a, 100, a, 100, 1, c, G.NTT_SCHED_PLAIN)
+        assert e.value.status == 1
+    with G.Plan(W.P_B, 16) as plan:
+        a = torch.zeros(1 << 15, dtype=torch.uint32, device="cuda")
+        c = torch.zeros(1 << 16, dtype=torch.uint32, device="cuda")
+        with pytest.raises(G.NttError) as e:
+            G.polymul_mod_p_batch(plan, a, 1 << 15, a, 1 << 15, 1, c)   # no workspace
+        assert e.value.status == 10
+    with G.Plan(W.P_A, 10, G.NTT_FLAG_CHECK) as plan:
+        bad = torch.full((100,), W.P_A, dtype=torch.uint32, device="cuda")
+        c = torch.zeros(199, dtype=torch.uint32, device="cuda")
+        with pytest.raises(G.NttError) as e:
+            G.polymul_mod_p_batch(plan, bad, 100, bad, 100, 1, c)
+        assert e.value.status == 6
