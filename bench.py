@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--plain-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default=None, choices=["fused"],
+                    help="run only the fused timed steps (for profiler captures)")
     return ap.parse_args()
 
 
@@ -356,8 +358,17 @@ def run_native(args, world, rank, local):
 
     for _ in range(max(3, args.warmup)):
         step_fused()
-        step_plain()
+        if args.only is None:
+            step_plain()
     torch.cuda.synchronize()
+
+    if args.only == "fused":
+        ms = timed_steps(step_fused, flush, args.steps, stream)
+        if rank == 0:
+            print(json.dumps({"only": "fused", "ms_per_step": sum(ms) / len(ms),
+                              "value": batch / (sum(ms) / len(ms) / 1e3), "unit": UNIT}))
+        plan.close()
+        return
 
     # ---- fused: the reported value
     clocks = ClockSampler(local)

@@ -84,13 +84,23 @@ __global__ void k_int_probe(uint32_t* out, int iters, int kind, uint32_t seed) {
             }
         }
     } else {
+        // add and xor alternate along each chain so no two consecutive
+        // operations can merge into one three-input instruction
         for (int i = 0; i < iters; ++i) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 4; ++u) {
                 asm volatile("add.u32 %0, %0, %1;" : "+r"(a0) : "r"(m));
                 asm volatile("add.u32 %0, %0, %1;" : "+r"(a1) : "r"(m));
                 asm volatile("add.u32 %0, %0, %1;" : "+r"(a2) : "r"(m));
                 asm volatile("add.u32 %0, %0, %1;" : "+r"(a3) : "r"(m));
+                asm volatile("add.u32 %0, %0, %1;" : "+r"(a4) : "r"(m));
+                asm volatile("add.u32 %0, %0, %1;" : "+r"(a5) : "r"(m));
+                asm volatile("add.u32 %0, %0, %1;" : "+r"(a6) : "r"(m));
+                asm volatile("add.u32 %0, %0, %1;" : "+r"(a7) : "r"(m));
+                asm volatile("xor.b32 %0, %0, %1;" : "+r"(a0) : "r"(c));
+                asm volatile("xor.b32 %0, %0, %1;" : "+r"(a1) : "r"(c));
+                asm volatile("xor.b32 %0, %0, %1;" : "+r"(a2) : "r"(c));
+                asm volatile("xor.b32 %0, %0, %1;" : "+r"(a3) : "r"(c));
                 asm volatile("xor.b32 %0, %0, %1;" : "+r"(a4) : "r"(c));
                 asm volatile("xor.b32 %0, %0, %1;" : "+r"(a5) : "r"(c));
                 asm volatile("xor.b32 %0, %0, %1;" : "+r"(a6) : "r"(c));
