@@ -158,6 +158,26 @@ int polymul_mod_p_batch(const ntt_plan* plan, const void* d_a, size_t na,
 int polymul_mod_p(const ntt_plan* plan, const void* d_a, size_t na, const void* d_b,
                   size_t nb, void* d_c, void* d_ws, size_t ws_bytes, void* stream);
 
+/* polymul_mod_p_batch with the fused schedule for callers that cannot
+ * allocate device memory when they need a product: code running while a
+ * stream is captured into a CUDA graph, host callbacks on a stream (which
+ * may not call the CUDA API), latency-critical loops that cannot afford an
+ * allocation's implicit synchronisation, and hosts that own all device
+ * memory through their own allocator.  The paper has no counterpart (its
+ * products run on the CPU).  Operands and output are as for
+ * polymul_mod_p_batch; the scratch space the larger transforms need comes
+ * from a fixed 32 MiB array inside the library (held on every GPU that loads
+ * the library until the process exits), so this call allocates nothing.
+ * Products needing more scratch than that (2 n word_bytes per product when
+ * n > 2^tile_max_log) return NTT_ERR_WORKSPACE.  The first call on each
+ * device looks up the array's address and must come before any stream
+ * capture.  Every call shares the one array: calls whose work overlaps on
+ * the GPU race and must be serialised by the caller.  The plan's device
+ * must be current. */
+int polymul_mod_p_batch_static(const ntt_plan* plan, const void* d_a, size_t na,
+                               const void* d_b, size_t nb, size_t batch, void* d_c,
+                               void* stream);
+
 /* ---- element-wise modular products (Sections 2.2, 2.3, 3.3) ----------- */
 
 /* z[i] = x[i] * y[i] rem p with the reduction `kind` (NTT_MM_*), on uint64

@@ -89,6 +89,7 @@ def _load():
             "polymul_workspace_size": (_sz, [_vp, _sz, _uint]),
             "polymul_mod_p_batch": (_int, [_vp, _vp, _sz, _vp, _sz, _sz, _vp, _uint, _vp, _sz, _vp]),
             "polymul_mod_p": (_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp]),
+            "polymul_mod_p_batch_static": (_int, [_vp, _vp, _sz, _vp, _sz, _sz, _vp, _vp]),
             "ntt_modmul_vec": (_int, [_u64, _uint, _uint, _vp, _vp, _vp, _vp, _sz, _vp]),
             "ntt_status_str": (ctypes.c_char_p, [_int]),
             "ntt_last_error": (ctypes.c_char_p, []),
@@ -227,6 +228,14 @@ def polymul_mod_p(plan: Plan, a, na: int, b, nb: int, c, ws=None, ws_bytes: int 
         ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
     _check(_load().polymul_mod_p(plan.handle, _ptr(a), na, _ptr(b), nb, _ptr(c), _ptr(ws),
                                  ws_bytes, _stream(stream)), "polymul_mod_p")
+
+
+def polymul_mod_p_batch_static(plan: Plan, a, na: int, b, nb: int, batch: int, c, stream=None):
+    """polymul_mod_p_batch (fused) with the library's fixed scratch array:
+    for callers that cannot allocate device memory (see include/gbntt.h)."""
+    _check(_load().polymul_mod_p_batch_static(plan.handle, _ptr(a), na, _ptr(b), nb, batch,
+                                              _ptr(c), _stream(stream)),
+           "polymul_mod_p_batch_static")
 
 
 def ntt_modmul_vec(p: int, kind: int, word_bytes: int, x, y, yc, z, n: int | None = None,
