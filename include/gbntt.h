@@ -67,6 +67,8 @@ enum ntt_status {
 #define NTT_MM_FMA 3u         /* Function 16 over IEEE double, p < 2^50 */
 #define NTT_MM_MONT_FIXED 4u  /* Remark 8: y fixed, companion phi; kernels' twiddle product */
 #define NTT_MM_MONT_PRODUCT 5u /* the kernels' general (pointwise) product: x y 2^-n rem p, scaled back */
+#define NTT_MM_ADD 6u         /* the kernels' modular sum x + y rem p (Section 2.1) */
+#define NTT_MM_SUB 7u         /* the kernels' modular difference x - y rem p */
 
 typedef struct ntt_plan ntt_plan;
 
@@ -178,9 +180,10 @@ int polymul_mod_p_batch_static(const ntt_plan* plan, const void* d_a, size_t na,
                                const void* d_b, size_t nb, size_t batch, void* d_c,
                                void* stream);
 
-/* ---- element-wise modular products (Sections 2.2, 2.3, 3.3) ----------- */
+/* ---- element-wise modular operations (Sections 2.1-2.3, 3.3) ----------- */
 
-/* z[i] = x[i] * y[i] rem p with the reduction `kind` (NTT_MM_*), on uint64
+/* z[i] = x[i] * y[i] rem p with the reduction `kind` (NTT_MM_*; kinds
+ * NTT_MM_ADD / NTT_MM_SUB give x[i] + y[i] and x[i] - y[i] rem p), on uint64
  * device arrays of residues < p.  word_bytes selects the 32- or 64-bit
  * implementation (4 needs p < 2^32).  NTT_MM_SHOUP / NTT_MM_MONT_FIXED read
  * the companions d_yc (from ntt_fixed_companion); other kinds ignore it.

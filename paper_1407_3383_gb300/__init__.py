@@ -34,6 +34,8 @@ NTT_MM_MONTGOMERY = 2
 NTT_MM_FMA = 3
 NTT_MM_MONT_FIXED = 4
 NTT_MM_MONT_PRODUCT = 5
+NTT_MM_ADD = 6
+NTT_MM_SUB = 7
 
 _lock = threading.Lock()
 _lib = None

@@ -62,7 +62,7 @@ struct DevPlan {
 template <class Ar>
 struct Hook {
     const typename Ar::tw* tab;
-    long long A, B, C, off;
+    int A, B, C, off;
 };
 
 template <int R>
@@ -119,7 +119,7 @@ struct PhaseGeom {
     int logL;
     int lognvec;
     int logX;
-    long long VS, XS, ES;
+    int VS, XS, ES;       // shared-memory word strides
     bool vfast;
 };
 
@@ -150,8 +150,8 @@ __device__ __forceinline__ void run_pass(const DevPlan<Ar>& P, typename Ar::word
         }
         const int j1 = k & ((1 << logMR) - 1);
         const int blk = k >> logMR;
-        word* b = s + v * g.VS + xl * g.XS + (long long)((blk << logM) + j1) * g.ES;
-        const long long st = (long long)(1 << logMR) * g.ES;
+        word* b = s + (v * g.VS + xl * g.XS + ((blk << logM) + j1) * g.ES);
+        const int st = (1 << logMR) * g.ES;
         word x[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) x[t] = b[t * st];
@@ -162,7 +162,7 @@ __device__ __forceinline__ void run_pass(const DevPlan<Ar>& P, typename Ar::word
             } else if (hook) {
 #pragma unroll
                 for (int t = 0; t < R; ++t) {
-                    long long pos = (blk << logM) + t;
+                    const int pos = (blk << logM) + t;
                     x[t] = P.ar.mulw(x[t], hook->tab[pos * hook->A + xl * hook->B + v * hook->C + hook->off]);
                 }
             }
@@ -175,7 +175,7 @@ __device__ __forceinline__ void run_pass(const DevPlan<Ar>& P, typename Ar::word
             } else if (hook) {
 #pragma unroll
                 for (int t = 0; t < R; ++t) {
-                    long long pos = (blk << logM) + t;
+                    const int pos = (blk << logM) + t;
                     x[t] = P.ar.mulw(x[t], hook->tab[pos * hook->A + xl * hook->B + v * hook->C + hook->off]);
                 }
             }
@@ -231,7 +231,7 @@ __device__ void phase_inv(const DevPlan<Ar>& P, typename Ar::word* s, const Phas
 struct VecLayout {
     int logL;
     int lognvec;
-    long long VS, RS, CS;
+    int VS, RS, CS;
     bool vfast;   // lanes over vectors first (VS == 1 layouts)
 };
 
@@ -239,10 +239,10 @@ __host__ __device__ inline int tile_l2(int logL) { return logL / 2; }
 __host__ __device__ inline int tile_l1(int logL) { return logL - logL / 2; }
 
 // Word offset of element i of vector v.
-__device__ __forceinline__ long long vec_addr(const VecLayout& L, int v, long long i) {
+__device__ __forceinline__ int vec_addr(const VecLayout& L, int v, int i) {
     if (L.logL <= kMaxLineLog) return v * L.VS + i * L.CS;
     const int l1 = tile_l1(L.logL);
-    return v * L.VS + (i >> l1) * L.RS + (i & ((1LL << l1) - 1)) * L.CS;
+    return v * L.VS + (i >> l1) * L.RS + (i & ((1 << l1) - 1)) * L.CS;
 }
 
 // Forward transform of every vector.  vhook (optional) is applied to
@@ -257,7 +257,7 @@ __device__ void vec_fwd(const DevPlan<Ar>& P, typename Ar::word* s, const VecLay
     }
     const int l2 = tile_l2(L.logL), l1 = tile_l1(L.logL);
     // column phase: lines (v, c) of length L2, tile twiddle at its end
-    Hook<Ar> th{P.tile_fwd[L.logL], 1LL << l1, 1, 0, 0};
+    Hook<Ar> th{P.tile_fwd[L.logL], 1 << l1, 1, 0, 0};
     PhaseGeom gc{l2, L.lognvec, l1, L.VS, L.CS, L.RS, L.vfast};
     phase_fwd<Ar>(P, s, gc, &th);
     // row phase: lines (v, r) of length L1; vector position = r*L1 + c
@@ -286,7 +286,7 @@ __device__ void vec_inv(const DevPlan<Ar>& P, typename Ar::word* s, const VecLay
     } else {
         phase_inv<Ar>(P, s, gr, nullptr);
     }
-    Hook<Ar> th{P.tile_inv[L.logL], 1LL << l1, 1, 0, 0};
+    Hook<Ar> th{P.tile_inv[L.logL], 1 << l1, 1, 0, 0};
     PhaseGeom gc{l2, L.lognvec, l1, L.VS, L.CS, L.RS, L.vfast};
     phase_inv<Ar>(P, s, gc, &th);
 }

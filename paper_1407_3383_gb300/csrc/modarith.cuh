@@ -16,8 +16,10 @@
 //    even when m = n and accepts any 32-bit x.  The general product (the
 //    pointwise step) is Function 13 on the full product x y, giving
 //    x y 2^-32 rem p; the 2^32 is folded into the final scaling.
-//    Addition is Function 4's max/compare form (valid for m = n), written
-//    with one compare: x + y rem p = x - (p - y), plus p when x < p - y.
+//    Every correction is one subtraction with borrow: x - y rem p is
+//    d = x - y (mod 2^32) plus p when x < y.  Addition is Function 4's form
+//    x + y rem p = x - (p - y) (valid for m = n); the Montgomery tails
+//    hi(x w~) - hi(q p) are the same subtraction.
 //
 //  * Shoup64 -- p < 2^62 in 64-bit words.  Fixed-multiplicand products use
 //    Function 8 with n = 64 and psi = floor(2^64 w / p) (Proposition 4: the
@@ -41,31 +43,26 @@ struct Mont32 {
     uint32_t p;      // odd modulus < 2^32
     uint32_t pinv;   // p^-1 rem 2^32
 
-    __device__ __forceinline__ uint32_t add(uint32_t x, uint32_t y) const {
-        uint32_t a = p - y;            // in (0, p]
-        uint32_t d = x - a;            // x + y - p (mod 2^32)
-        return (x >= a) ? d : d + p;
-    }
+    // x - y rem p for x < p, y <= p.
     __device__ __forceinline__ uint32_t sub(uint32_t x, uint32_t y) const {
-        uint32_t d = x - y;
-        return (x >= y) ? d : d + p;
+        const uint32_t d = x - y;
+        return d + ((x < y) ? p : 0u);
     }
+    __device__ __forceinline__ uint32_t add(uint32_t x, uint32_t y) const { return sub(x, p - y); }
     // x * w rem p for any 32-bit x; t = (w 2^32 rem p, (w 2^32 rem p) p^-1 rem 2^32).
     __device__ __forceinline__ uint32_t mulw(uint32_t x, Tw32 t) const {
-        uint32_t q = x * t.c;
-        uint32_t h = __umulhi(x, t.w);
-        uint32_t l = __umulhi(q, p);
-        uint32_t r = h - l;
-        return (h >= l) ? r : r + p;
+        const uint32_t q = x * t.c;
+        const uint32_t h = __umulhi(x, t.w);   // < p
+        const uint32_t l = __umulhi(q, p);     // < p
+        return sub(h, l);
     }
     // x * y * 2^-32 rem p for x, y < p.
     __device__ __forceinline__ uint32_t mulmont(uint32_t x, uint32_t y) const {
-        uint32_t lo = x * y;
-        uint32_t hi = __umulhi(x, y);
-        uint32_t q = lo * pinv;
-        uint32_t l = __umulhi(q, p);
-        uint32_t r = hi - l;
-        return (hi >= l) ? r : r + p;
+        const uint32_t lo = x * y;
+        const uint32_t hi = __umulhi(x, y);
+        const uint32_t q = lo * pinv;
+        const uint32_t l = __umulhi(q, p);
+        return sub(hi, l);
     }
 };
 

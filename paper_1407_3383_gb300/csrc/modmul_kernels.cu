@@ -9,6 +9,7 @@
 //  FMA          Function 16 over IEEE double (m <= 50, Proposition 13)
 //  Mont-fixed   the 32-bit kernels' twiddle product (Remark 8 form)
 //  Mont-product the kernels' pointwise product (x y 2^-n rem p)
+//  add / sub    the kernels' modular sum and difference (Section 2.1)
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -146,6 +147,16 @@ __global__ void k_modmul_vec(MMArgs A, const uint64_t* __restrict__ x, const uin
                     r = ar.mulmont(ar.mulmont(x32, y32), static_cast<uint32_t>(A.r2));
                     break;
                 }
+                case NTT_MM_ADD: {
+                    const Mont32 ar{p, static_cast<uint32_t>(A.pinv)};
+                    r = ar.add(x32, y32);
+                    break;
+                }
+                case NTT_MM_SUB: {
+                    const Mont32 ar{p, static_cast<uint32_t>(A.pinv)};
+                    r = ar.sub(x32, y32);
+                    break;
+                }
                 default:
                     r = fma_mulmod(static_cast<double>(xi), static_cast<double>(yi), A.dp, A.u);
             }
@@ -172,6 +183,12 @@ __global__ void k_modmul_vec(MMArgs A, const uint64_t* __restrict__ x, const uin
                     r = ar.mulmont(ar.mulmont(xi, yi), A.r2);
                     break;
                 }
+                case NTT_MM_ADD:
+                    r = Shoup64{p, A.pinv}.add(xi, yi);
+                    break;
+                case NTT_MM_SUB:
+                    r = Shoup64{p, A.pinv}.sub(xi, yi);
+                    break;
                 default:
                     r = fma_mulmod(static_cast<double>(xi), static_cast<double>(yi), A.dp, A.u);
             }
@@ -182,7 +199,7 @@ __global__ void k_modmul_vec(MMArgs A, const uint64_t* __restrict__ x, const uin
 
 int launch_modmul_vec(uint64_t p, unsigned kind, unsigned word_bytes, const uint64_t* x,
                       const uint64_t* y, const uint64_t* yc, uint64_t* z, size_t n, cudaStream_t st) {
-    if (kind > NTT_MM_MONT_PRODUCT || (word_bytes != 4 && word_bytes != 8)) return NTT_ERR_ARG;
+    if (kind > NTT_MM_SUB || (word_bytes != 4 && word_bytes != 8)) return NTT_ERR_ARG;
     if (p < 3 || (p & 1) == 0 || (p >> 63)) return NTT_ERR_MODULUS;
     if (word_bytes == 4 && (p >> 32)) return NTT_ERR_MODULUS;
     if (word_bytes == 8 && (p >> 62) && kind != NTT_MM_MONTGOMERY && kind != NTT_MM_BARRETT)

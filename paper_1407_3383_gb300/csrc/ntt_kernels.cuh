@@ -38,10 +38,10 @@ __host__ __device__ inline VecLayout tile_layout(int logL, int lognvec) {
     if (logL <= kMaxLineLog) {
         L.CS = 1;
         L.RS = 0;
-        L.VS = (1LL << logL) + 1;
+        L.VS = (1 << logL) + 1;
         L.vfast = true;
     } else {
-        const long long L1 = 1LL << tile_l1(logL), L2 = 1LL << tile_l2(logL);
+        const int L1 = 1 << tile_l1(logL), L2 = 1 << tile_l2(logL);
         L.CS = 1;
         L.RS = L1 + 1;
         L.VS = L2 * L.RS;
@@ -51,26 +51,26 @@ __host__ __device__ inline VecLayout tile_layout(int logL, int lognvec) {
 }
 
 __host__ __device__ inline long long layout_words(const VecLayout& L) {
-    return (1LL << L.lognvec) * L.VS;
+    return (1LL << L.lognvec) * static_cast<long long>(L.VS);
 }
 
 // w columns (vectors) of length 2^logL, element i of column v at v + i*(w+1)
 // (with one extra word per tile row when the column is itself a tile).
 __host__ __device__ inline VecLayout slab_layout(int logL, int logw) {
     VecLayout L{};
-    const long long w = 1LL << logw;
+    const int w = 1 << logw;
     L.logL = logL;
     L.lognvec = logw;
     L.VS = 1;
     L.CS = w + 1;
     L.vfast = true;
-    if (logL > kMaxLineLog) L.RS = (1LL << tile_l1(logL)) * (w + 1) + 1;
+    if (logL > kMaxLineLog) L.RS = (1 << tile_l1(logL)) * (w + 1) + 1;
     return L;
 }
 
 __host__ __device__ inline long long slab_words(const VecLayout& L) {
-    if (L.logL <= kMaxLineLog) return (1LL << L.logL) * L.CS;
-    return (1LL << tile_l2(L.logL)) * L.RS;
+    if (L.logL <= kMaxLineLog) return (1LL << L.logL) * static_cast<long long>(L.CS);
+    return (1LL << tile_l2(L.logL)) * static_cast<long long>(L.RS);
 }
 
 // ------------------------------------------------------------------ fused kernels
@@ -97,15 +97,15 @@ k_tile_polymul(DevPlan<Ar> P, const typename Ar::word* __restrict__ a, long long
             if (i < na) xa = a[prod * na + i];
             if (i < nb) xb = b[prod * nb + i];
         }
-        sm[vec_addr(LA, v, i)] = xa;
-        sm[vec_addr(LA, v + ppc, i)] = xb;
+        sm[vec_addr(LA, v, static_cast<int>(i))] = xa;
+        sm[vec_addr(LA, v + ppc, static_cast<int>(i))] = xb;
     }
     __syncthreads();
     vec_fwd<Ar>(P, sm, LA, nullptr);
     for (long long idx = threadIdx.x; idx < (L << lppc); idx += blockDim.x) {
         const int v = static_cast<int>(idx >> logL);
         const long long i = idx & (L - 1);
-        const long long pa = vec_addr(LA, v, i), pb = vec_addr(LA, v + ppc, i);
+        const long long pa = vec_addr(LA, v, static_cast<int>(i)), pb = vec_addr(LA, v + ppc, static_cast<int>(i));
         sm[pa] = P.ar.mulmont(sm[pa], sm[pb]);
     }
     __syncthreads();
@@ -116,7 +116,7 @@ k_tile_polymul(DevPlan<Ar> P, const typename Ar::word* __restrict__ a, long long
         const int v = static_cast<int>(idx / nc);
         const long long i = idx - v * nc;
         const long long prod = prod0 + v;
-        if (prod < batch) c[prod * nc + i] = P.ar.mulw(sm[vec_addr(LC, v, i)], scale);
+        if (prod < batch) c[prod * nc + i] = P.ar.mulw(sm[vec_addr(LC, v, static_cast<int>(i))], scale);
     }
 }
 
@@ -134,7 +134,7 @@ k_tile_ntt(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long batch,
         const int v = static_cast<int>(idx >> logL);
         const long long i = idx & (L - 1);
         const long long prod = prod0 + v;
-        sm[vec_addr(LA, v, i)] = (prod < batch) ? data[prod * L + i] : word(0);
+        sm[vec_addr(LA, v, static_cast<int>(i))] = (prod < batch) ? data[prod * L + i] : word(0);
     }
     __syncthreads();
     if (FWD)
@@ -146,7 +146,7 @@ k_tile_ntt(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long batch,
         const long long i = idx & (L - 1);
         const long long prod = prod0 + v;
         if (prod < batch) {
-            word x = sm[vec_addr(LA, v, i)];
+            word x = sm[vec_addr(LA, v, static_cast<int>(i))];
             data[prod * L + i] = FWD ? x : P.ar.mulw(x, scale);
         }
     }
@@ -176,15 +176,15 @@ k_col_fwd(DevPlan<Ar> P, const typename Ar::word* src0, long long len0,
         const long long row = idx >> logw;
         const int col = static_cast<int>(idx & (w - 1));
         const long long e = row * n1 + c0 + col;
-        sm[vec_addr(L, col, row)] = (e < len) ? src[prod * len + e] : word(0);
+        sm[vec_addr(L, col, static_cast<int>(row))] = (e < len) ? src[prod * len + e] : word(0);
     }
     __syncthreads();
-    Hook<Ar> h{P.glob_fwd, n1, 0, 1, c0};
+    Hook<Ar> h{P.glob_fwd, static_cast<int>(n1), 0, 1, static_cast<int>(c0)};
     vec_fwd<Ar>(P, sm, L, &h);
     for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const long long row = idx >> logw;
         const int col = static_cast<int>(idx & (w - 1));
-        out[row * n1 + c0 + col] = sm[vec_addr(L, col, row)];
+        out[row * n1 + c0 + col] = sm[vec_addr(L, col, static_cast<int>(row))];
     }
 }
 
@@ -209,16 +209,16 @@ k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
     for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const long long row = idx >> logw;
         const int col = static_cast<int>(idx & (w - 1));
-        sm[vec_addr(L, col, row)] = in[row * n1 + c0 + col];
+        sm[vec_addr(L, col, static_cast<int>(row))] = in[row * n1 + c0 + col];
     }
     __syncthreads();
-    Hook<Ar> h{P.glob_inv, n1, 0, 1, c0};
+    Hook<Ar> h{P.glob_inv, static_cast<int>(n1), 0, 1, static_cast<int>(c0)};
     vec_inv<Ar>(P, sm, L, &h);
     for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const long long row = idx >> logw;
         const int col = static_cast<int>(idx & (w - 1));
         const long long e = row * n1 + c0 + col;
-        if (e < out_len) dst[prod * out_len + e] = P.ar.mulw(sm[vec_addr(L, col, row)], scale);
+        if (e < out_len) dst[prod * out_len + e] = P.ar.mulw(sm[vec_addr(L, col, static_cast<int>(row))], scale);
     }
 }
 
@@ -244,14 +244,14 @@ k_row_polymul(DevPlan<Ar> P, typename Ar::word* ws, long long ws_stride, int log
         const long long i = idx & (n1 - 1);
         const int arr = v >> lrpc;
         const long long row = r0 + (v & (rpc - 1));
-        sm[vec_addr(L, v, i)] = base[arr * N + row * n1 + i];
+        sm[vec_addr(L, v, static_cast<int>(i))] = base[arr * N + row * n1 + i];
     }
     __syncthreads();
     vec_fwd<Ar>(P, sm, L, nullptr);
     for (long long idx = threadIdx.x; idx < (static_cast<long long>(rpc) << k1); idx += blockDim.x) {
         const int v = static_cast<int>(idx >> k1);
         const long long i = idx & (n1 - 1);
-        const long long pa = vec_addr(L, v, i), pb = vec_addr(L, v + rpc, i);
+        const long long pa = vec_addr(L, v, static_cast<int>(i)), pb = vec_addr(L, v + rpc, static_cast<int>(i));
         sm[pa] = P.ar.mulmont(sm[pa], sm[pb]);
     }
     __syncthreads();
@@ -260,7 +260,7 @@ k_row_polymul(DevPlan<Ar> P, typename Ar::word* ws, long long ws_stride, int log
     for (long long idx = threadIdx.x; idx < (static_cast<long long>(rpc) << k1); idx += blockDim.x) {
         const int v = static_cast<int>(idx >> k1);
         const long long i = idx & (n1 - 1);
-        base[(r0 + v) * n1 + i] = sm[vec_addr(LC, v, i)];
+        base[(r0 + v) * n1 + i] = sm[vec_addr(LC, v, static_cast<int>(i))];
     }
 }
 
@@ -280,7 +280,7 @@ k_row_ntt(DevPlan<Ar> P, typename Ar::word* data, int logN, int k2, int lrpc, lo
     for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int v = static_cast<int>(idx >> k1);
         const long long i = idx & (n1 - 1);
-        sm[vec_addr(L, v, i)] = base[(r0 + v) * n1 + i];
+        sm[vec_addr(L, v, static_cast<int>(i))] = base[(r0 + v) * n1 + i];
     }
     __syncthreads();
     if (FWD)
@@ -290,7 +290,7 @@ k_row_ntt(DevPlan<Ar> P, typename Ar::word* data, int logN, int k2, int lrpc, lo
     for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int v = static_cast<int>(idx >> k1);
         const long long i = idx & (n1 - 1);
-        base[(r0 + v) * n1 + i] = sm[vec_addr(L, v, i)];
+        base[(r0 + v) * n1 + i] = sm[vec_addr(L, v, static_cast<int>(i))];
     }
 }
 

@@ -43,15 +43,24 @@ def _run(p, kind, wb, x, y):
 
 
 KINDS32 = [G.NTT_MM_BARRETT, G.NTT_MM_SHOUP, G.NTT_MM_MONTGOMERY, G.NTT_MM_MONT_FIXED,
-           G.NTT_MM_MONT_PRODUCT, G.NTT_MM_FMA]
-KINDS64 = [G.NTT_MM_BARRETT, G.NTT_MM_SHOUP, G.NTT_MM_MONTGOMERY, G.NTT_MM_MONT_PRODUCT]
+           G.NTT_MM_MONT_PRODUCT, G.NTT_MM_FMA, G.NTT_MM_ADD, G.NTT_MM_SUB]
+KINDS64 = [G.NTT_MM_BARRETT, G.NTT_MM_SHOUP, G.NTT_MM_MONTGOMERY, G.NTT_MM_MONT_PRODUCT,
+           G.NTT_MM_ADD, G.NTT_MM_SUB]
+
+
+def _want(p, kind, x, y):
+    if kind == G.NTT_MM_ADD:
+        return np.array([O.addmod(int(a), int(b), p) for a, b in zip(x, y)], dtype=np.uint64)
+    if kind == G.NTT_MM_SUB:
+        return np.array([O.submod(int(a), int(b), p) for a, b in zip(x, y)], dtype=np.uint64)
+    return O.mulmod_vec(p, x, y)
 
 
 @pytest.mark.parametrize("p", P32)
 @pytest.mark.parametrize("kind", KINDS32)
 def test_modmul_u32(p, kind):
-    x, y = _operands(p, 1 << 18, p ^ kind)
-    assert (_run(p, kind, 4, x, y) == O.mulmod_vec(p, x, y)).all()
+    x, y = _operands(p, 1 << 16 if kind >= G.NTT_MM_ADD else 1 << 18, p ^ kind)
+    assert (_run(p, kind, 4, x, y) == _want(p, kind, x, y)).all()
 
 
 @pytest.mark.parametrize("p", P64)
@@ -59,15 +68,18 @@ def test_modmul_u32(p, kind):
 def test_modmul_u64(p, kind):
     if kind == G.NTT_MM_FMA and p >= (1 << 50):
         pytest.skip("Function 16 needs m <= 50 (Proposition 13)")
-    x, y = _operands(p, 1 << 18, p ^ (kind + 7))
-    assert (_run(p, kind, 8, x, y) == O.mulmod_vec(p, x, y)).all()
+    x, y = _operands(p, 1 << 16 if kind >= G.NTT_MM_ADD else 1 << 18, p ^ (kind + 7))
+    assert (_run(p, kind, 8, x, y) == _want(p, kind, x, y)).all()
 
 
 @pytest.mark.parametrize("p", [17, 257, 7681])
 @pytest.mark.parametrize("kind", KINDS32)
 def test_modmul_exhaustive_small_primes(p, kind):
+    if kind >= G.NTT_MM_ADD and p > 257:
+        pytest.skip("sums and differences: exhaustive on the smaller primes")
     x = np.repeat(np.arange(p, dtype=np.uint64), p)
     y = np.tile(np.arange(p, dtype=np.uint64), p)
-    assert (_run(p, kind, 4, x, y) == O.mulmod_vec(p, x, y)).all()
+    want = _want(p, kind, x, y)
+    assert (_run(p, kind, 4, x, y) == want).all()
     if kind in KINDS64:
-        assert (_run(p, kind, 8, x, y) == O.mulmod_vec(p, x, y)).all()
+        assert (_run(p, kind, 8, x, y) == want).all()
