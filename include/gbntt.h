@@ -180,6 +180,32 @@ int polymul_mod_p_batch_static(const ntt_plan* plan, const void* d_a, size_t na,
                                const void* d_b, size_t nb, size_t batch, void* d_c,
                                void* stream);
 
+/* ---- integer products (Section 5.3) ------------------------------------- */
+
+typedef struct intmul_plan intmul_plan;
+
+/* Plan for products of integers of up to max_limbs 32-bit limbs each: the
+ * three primes P1 < P2 < P3 = the first three k 2^40 + 1 above 2^61
+ * (ntt_find_prime(62, 40, i)), a transform plan per prime for every length
+ * 2^1 .. 2^k the largest product needs, and the Garner constants.  Builds
+ * all tables up front (this call allocates; intmul_crt does not).
+ * NTT_ERR_SIZE if a product would need transforms above 2^24. */
+int intmul_plan_create(size_t max_limbs, intmul_plan** out);
+int intmul_plan_destroy(intmul_plan* plan);
+
+/* Workspace bytes intmul_crt needs for operands of na and nb limbs. */
+size_t intmul_workspace_size(const intmul_plan* plan, size_t na, size_t nb);
+
+/* c = a * b for non-negative integers in little-endian 32-bit limbs:
+ * a has na >= 1 limbs, b has nb >= 1, c receives exactly na + nb limbs.
+ * Kronecker segmentation into h = 64-bit chunks, the product modulo each of
+ * the three primes (two forward transforms, pointwise product, inverse),
+ * Garner reconstruction of every coefficient (exact: coefficients are below
+ * 2^150 < P1 P2 P3) and carry propagation (Section 5.3).  d_ws: at least
+ * intmul_workspace_size bytes, 256-byte aligned.  Asynchronous on stream. */
+int intmul_crt(const intmul_plan* plan, const uint32_t* d_a, size_t na, const uint32_t* d_b,
+               size_t nb, uint32_t* d_c, void* d_ws, size_t ws_bytes, void* stream);
+
 /* ---- element-wise modular operations (Sections 2.1-2.3, 3.3) ----------- */
 
 /* z[i] = x[i] * y[i] rem p with the reduction `kind` (NTT_MM_*; kinds

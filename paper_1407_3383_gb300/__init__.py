@@ -93,6 +93,10 @@ def _load():
             "polymul_mod_p": (_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp]),
             "polymul_mod_p_batch_static": (_int, [_vp, _vp, _sz, _vp, _sz, _sz, _vp, _vp]),
             "ntt_modmul_vec": (_int, [_u64, _uint, _uint, _vp, _vp, _vp, _vp, _sz, _vp]),
+            "intmul_plan_create": (_int, [_sz, ctypes.POINTER(_vp)]),
+            "intmul_plan_destroy": (_int, [_vp]),
+            "intmul_workspace_size": (_sz, [_vp, _sz, _sz]),
+            "intmul_crt": (_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp]),
             "ntt_status_str": (ctypes.c_char_p, [_int]),
             "ntt_last_error": (ctypes.c_char_p, []),
             "ntt_version": (ctypes.c_char_p, []),
@@ -245,6 +249,51 @@ def ntt_modmul_vec(p: int, kind: int, word_bytes: int, x, y, yc, z, n: int | Non
     n = x.numel() if n is None else n
     _check(_load().ntt_modmul_vec(p, kind, word_bytes, _ptr(x), _ptr(y), _ptr(yc), _ptr(z), n,
                                   _stream(stream)), "ntt_modmul_vec")
+
+
+# ---------------------------------------------------------------- integer products
+
+class IntmulPlan:
+    """An intmul_plan: three 62-bit primes and their transform plans."""
+
+    def __init__(self, max_limbs: int):
+        h = _vp()
+        _check(_load().intmul_plan_create(max_limbs, ctypes.byref(h)), "intmul_plan_create")
+        self.handle = h.value
+        self.max_limbs = max_limbs
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _load().intmul_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def intmul_plan_create(max_limbs: int) -> IntmulPlan:
+    return IntmulPlan(max_limbs)
+
+
+def intmul_workspace_size(plan: IntmulPlan, na: int, nb: int) -> int:
+    return int(_load().intmul_workspace_size(plan.handle, na, nb))
+
+
+def intmul_crt(plan: IntmulPlan, a, na: int, b, nb: int, c, ws, ws_bytes: int | None = None,
+               stream=None):
+    if ws_bytes is None:
+        ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    _check(_load().intmul_crt(plan.handle, _ptr(a), na, _ptr(b), nb, _ptr(c), _ptr(ws), ws_bytes,
+                              _stream(stream)), "intmul_crt")
 
 
 # ---------------------------------------------------------------- conveniences
