@@ -204,7 +204,7 @@ k_carry_apply(long long nwords, uint32_t* __restrict__ c, long long nlimbs,
         const uint8_t s = st[j];
         const uint32_t cin = (s == kGen) ? 1u : (s == kProp ? blk_carry[j / kCarryBlock] : 0u);
         if (!cin) continue;
-        uint64_t v = c[2 * j];
+        uint64_t v = (2 * j < nlimbs) ? c[2 * j] : 0u;
         if (2 * j + 1 < nlimbs) v |= static_cast<uint64_t>(c[2 * j + 1]) << 32;
         store_word(c, nlimbs, j, v + 1);
     }
