@@ -180,6 +180,68 @@ int polymul_mod_p_batch_static(const ntt_plan* plan, const void* d_a, size_t na,
                                const void* d_b, size_t nb, size_t batch, void* d_c,
                                void* stream);
 
+/* ---- uneven batches with mixed moduli ------------------------------------ */
+
+/* One product of an uneven batch: operands a[a_off .. a_off+na) and
+ * b[b_off .. b_off+nb), output c[c_off .. c_off+na+nb-1), offsets in words
+ * into the run's flat buffers; `prime` indexes the plan's modulus list. */
+typedef struct polymul_desc {
+    uint64_t a_off, b_off, c_off;
+    uint32_t na, nb;
+    uint32_t prime;
+    uint32_t reserved;
+} polymul_desc;
+
+/* Run modes of polymul_batch_run. */
+#define NTT_BATCH_DIRECT 0u   /* every launch on the caller's stream, in order */
+#define NTT_BATCH_STREAMS 1u  /* buckets spread over internal streams, joined back */
+#define NTT_BATCH_GRAPH 2u    /* the STREAMS work captured once into a CUDA graph, replayed */
+
+typedef struct polymul_batch_plan polymul_batch_plan;
+
+/* Plan `count` products of uneven lengths over up to 64 moduli (all below
+ * 2^32, or all in [2^32, 2^62)).  Host descriptors are read once.  Each
+ * product's transform length is the least 2^k >= na + nb - 1.  Products
+ * with 2^k within one thread block become items of a persistent kernel
+ * that takes them from a ticket counter (largest first, up to 16 equal-size
+ * equal-modulus products per item); longer products are grouped by
+ * (modulus, k) and run as the fused three-pass schedule.  Allocates the
+ * transform plans and the device descriptor tables (not a hot call).
+ * flags: reserved, pass 0. */
+int polymul_batch_plan_create(const uint64_t* primes, unsigned nprimes, const polymul_desc* h_desc,
+                              size_t count, unsigned flags, polymul_batch_plan** out);
+int polymul_batch_plan_destroy(polymul_batch_plan* plan);
+
+/* Workspace bytes polymul_batch_run needs (the ticket counter and the
+ * long products' transformed operands). */
+size_t polymul_batch_workspace_size(const polymul_batch_plan* plan);
+
+/* Every product of the plan, reading d_a / d_b and writing d_c at the
+ * descriptors' offsets (device buffers, words of the plan's size).  mode:
+ * NTT_BATCH_*.  In NTT_BATCH_GRAPH mode the first run with a given set of
+ * (d_a, d_b, d_c, d_ws) captures the work into a CUDA graph (allocating the
+ * graph); later runs with the same pointers only launch it.  Not thread-safe
+ * for one plan. */
+int polymul_batch_run(polymul_batch_plan* plan, const void* d_a, const void* d_b, void* d_c,
+                      void* d_ws, size_t ws_bytes, unsigned mode, void* stream);
+
+/* ---- launch-shape autotuning ------------------------------------------------ */
+
+/* Time the candidate launch shapes of the fused product for this plan's
+ * transform length on `batch` products of length n/2 (temporary device
+ * buffers are allocated) and keep the fastest in the process-wide shape
+ * table used by every later launch of that (word size, log2 n).  Writes the
+ * best time in ms to *best_ms when non-null.  Synchronous. */
+int ntt_autotune(const ntt_plan* plan, size_t batch, void* stream, float* best_ms);
+/* The shape currently used for (word_bytes, log2n): products per block,
+ * columns per block and rows per block, each as log2. */
+int ntt_tune_get(unsigned word_bytes, unsigned log2n, int* lppc, int* logw, int* lrpc);
+/* Text form of the shape table ("word_bytes log2n lppc logw lrpc" lines):
+ * export into buf (cap bytes; *len receives the length; buf may be NULL to
+ * query it) and import such text back. */
+int ntt_tune_export(char* buf, size_t cap, size_t* len);
+int ntt_tune_import(const char* text);
+
 /* ---- integer products (Section 5.3) ------------------------------------- */
 
 typedef struct intmul_plan intmul_plan;

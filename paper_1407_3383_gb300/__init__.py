@@ -36,6 +36,9 @@ NTT_MM_MONT_FIXED = 4
 NTT_MM_MONT_PRODUCT = 5
 NTT_MM_ADD = 6
 NTT_MM_SUB = 7
+NTT_BATCH_DIRECT = 0
+NTT_BATCH_STREAMS = 1
+NTT_BATCH_GRAPH = 2
 
 _lock = threading.Lock()
 _lib = None
@@ -93,6 +96,15 @@ def _load():
             "polymul_mod_p": (_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp]),
             "polymul_mod_p_batch_static": (_int, [_vp, _vp, _sz, _vp, _sz, _sz, _vp, _vp]),
             "ntt_modmul_vec": (_int, [_u64, _uint, _uint, _vp, _vp, _vp, _vp, _sz, _vp]),
+            "polymul_batch_plan_create": (_int, [_vp, _uint, _vp, _sz, _uint, ctypes.POINTER(_vp)]),
+            "polymul_batch_plan_destroy": (_int, [_vp]),
+            "polymul_batch_workspace_size": (_sz, [_vp]),
+            "polymul_batch_run": (_int, [_vp, _vp, _vp, _vp, _vp, _sz, _uint, _vp]),
+            "ntt_autotune": (_int, [_vp, _sz, _vp, ctypes.POINTER(ctypes.c_float)]),
+            "ntt_tune_get": (_int, [_uint, _uint, ctypes.POINTER(_int), ctypes.POINTER(_int),
+                                    ctypes.POINTER(_int)]),
+            "ntt_tune_export": (_int, [ctypes.c_char_p, _sz, ctypes.POINTER(_sz)]),
+            "ntt_tune_import": (_int, [ctypes.c_char_p]),
             "intmul_plan_create": (_int, [_sz, ctypes.POINTER(_vp)]),
             "intmul_plan_destroy": (_int, [_vp]),
             "intmul_workspace_size": (_sz, [_vp, _sz, _sz]),
@@ -249,6 +261,97 @@ def ntt_modmul_vec(p: int, kind: int, word_bytes: int, x, y, yc, z, n: int | Non
     n = x.numel() if n is None else n
     _check(_load().ntt_modmul_vec(p, kind, word_bytes, _ptr(x), _ptr(y), _ptr(yc), _ptr(z), n,
                                   _stream(stream)), "ntt_modmul_vec")
+
+
+# ---------------------------------------------------------------- uneven batches
+
+class PolymulDesc(ctypes.Structure):
+    _fields_ = [("a_off", _u64), ("b_off", _u64), ("c_off", _u64), ("na", _u32), ("nb", _u32),
+                ("prime", _u32), ("reserved", _u32)]
+
+
+class BatchPlan:
+    """A polymul_batch_plan over `primes` for products given as arrays of
+    operand lengths na, nb and modulus indices; operands and outputs are laid
+    out back to back in the order given (offsets in words)."""
+
+    def __init__(self, primes, na, nb, prime_idx):
+        import numpy as np
+        na = np.asarray(na, dtype=np.int64)
+        nb = np.asarray(nb, dtype=np.int64)
+        pi = np.asarray(prime_idx, dtype=np.int64)
+        count = na.size
+        nc = na + nb - 1
+        self.a_off = np.concatenate([[0], np.cumsum(na)[:-1]]).astype(np.int64)
+        self.b_off = np.concatenate([[0], np.cumsum(nb)[:-1]]).astype(np.int64)
+        self.c_off = np.concatenate([[0], np.cumsum(nc)[:-1]]).astype(np.int64)
+        self.na, self.nb, self.nc, self.prime_idx = na, nb, nc, pi
+        self.a_words, self.b_words, self.c_words = int(na.sum()), int(nb.sum()), int(nc.sum())
+        descs = (PolymulDesc * max(1, count))()
+        for t in range(count):
+            descs[t] = PolymulDesc(int(self.a_off[t]), int(self.b_off[t]), int(self.c_off[t]),
+                                   int(na[t]), int(nb[t]), int(pi[t]), 0)
+        arr = (_u64 * len(primes))(*[int(p) for p in primes])
+        h = _vp()
+        _check(_load().polymul_batch_plan_create(ctypes.cast(arr, _vp), len(primes),
+                                                 ctypes.cast(descs, _vp), count, 0, ctypes.byref(h)),
+               "polymul_batch_plan_create")
+        self.handle = h.value
+        self.primes = [int(p) for p in primes]
+        self.word_bytes = 8 if max(self.primes) >> 32 else 4
+        self.count = count
+
+    def workspace_size(self) -> int:
+        return int(_load().polymul_batch_workspace_size(self.handle))
+
+    def run(self, a, b, c, ws, mode: int = NTT_BATCH_GRAPH, stream=None):
+        ws_bytes = ws.numel() * ws.element_size()
+        _check(_load().polymul_batch_run(self.handle, _ptr(a), _ptr(b), _ptr(c), _ptr(ws), ws_bytes,
+                                         mode, _stream(stream)), "polymul_batch_run")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _load().polymul_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---------------------------------------------------------------- autotuning
+
+def ntt_autotune(plan: Plan, batch: int, stream=None) -> float:
+    best = ctypes.c_float()
+    _check(_load().ntt_autotune(plan.handle, batch, _stream(stream), ctypes.byref(best)), "ntt_autotune")
+    return best.value
+
+
+def ntt_tune_get(word_bytes: int, log2n: int) -> tuple[int, int, int]:
+    a, b, c = _int(), _int(), _int()
+    _check(_load().ntt_tune_get(word_bytes, log2n, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "ntt_tune_get")
+    return a.value, b.value, c.value
+
+
+def ntt_tune_export() -> str:
+    n = _sz()
+    _check(_load().ntt_tune_export(None, 0, ctypes.byref(n)), "ntt_tune_export")
+    buf = ctypes.create_string_buffer(n.value + 1)
+    _check(_load().ntt_tune_export(buf, n.value + 1, ctypes.byref(n)), "ntt_tune_export")
+    return buf.value.decode()
+
+
+def ntt_tune_import(text: str):
+    _check(_load().ntt_tune_import(text.encode()), "ntt_tune_import")
 
 
 # ---------------------------------------------------------------- integer products

@@ -56,6 +56,26 @@ struct DevPlan {
     const tw* plain_inv;
 };
 
+// One product of an uneven batch: word offsets of its operands and output in
+// the batch's flat buffers, and the operand lengths.
+struct BatchDesc {
+    unsigned long long aoff, boff, coff;
+    unsigned na, nb;
+};
+
+// A work item of the persistent kernel: `count` products (descriptors
+// desc[first .. first+count)) of one-block size 2^logL with modulus `prime`
+// (index into the plan array), final scaling `scale`.
+template <class Ar>
+struct SmallItem {
+    unsigned first, count, prime, logL;
+    typename Ar::tw scale;
+};
+
+constexpr int kSmallMaxPerItem = 16;
+
+__host__ __device__ inline int small_lppc(int logL) { return logL <= kMaxLineLog ? 4 : 0; }
+
 // Twiddle applied to every element of a vector at the outer end of a phase:
 // element at position `pos` of line `x` of vector `v` is multiplied by
 // tab[pos*A + x*B + v*C + off].

@@ -23,10 +23,39 @@ int launch_polymul_plain(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
                          cudaStream_t st);
 
 template <class Ar>
+int launch_batch_small(const DevPlan<Ar>* d_plans, const BatchDesc* d_desc, const void* d_items,
+                       unsigned nitems, unsigned* d_ticket, const typename Ar::word* a,
+                       const typename Ar::word* b, typename Ar::word* c, size_t smem, int grid,
+                       cudaStream_t st);
+
+template <class Ar>
+int batch_small_occupancy(size_t smem);
+
+template <class Ar>
+int launch_batch_bucket(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
+                        const typename Ar::word* b, typename Ar::word* c, const BatchDesc* d_desc,
+                        long long count, typename Ar::word* ws, typename Ar::tw scale,
+                        cudaStream_t st);
+
+template <class Ar>
 int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* data, long long batch,
                bool fwd, typename Ar::tw scale, cudaStream_t st);
 
 size_t polymul_ws_bytes(const ntt_plan* plan, size_t batch, unsigned schedule);
+
+// Launch shape of the fused product kernels for one (word size, log2 n):
+// lppc  log2 of products per block (one-block sizes),
+// logw  log2 of columns per block in the column passes,
+// lrpc  log2 of rows per block in the row pass.
+struct LaunchCfg {
+    int lppc, logw, lrpc;
+};
+LaunchCfg default_launch_cfg(unsigned word_bytes, int log2n, int tile_max_log);
+LaunchCfg launch_cfg(unsigned word_bytes, int log2n, int tile_max_log);   // tuned or default
+void set_launch_cfg(unsigned word_bytes, int log2n, LaunchCfg cfg);
+void clear_launch_cfg(unsigned word_bytes, int log2n);
+size_t col_smem_bytes(unsigned word_bytes, int k2, int logw);
+size_t tile_smem_bytes(unsigned word_bytes, int logL, int lognvec);
 
 // Launch profiling hooks (no-ops unless ntt_profile_begin() is active).
 void prof_begin_call(cudaStream_t st);

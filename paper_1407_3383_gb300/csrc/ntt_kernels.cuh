@@ -153,12 +153,15 @@ k_tile_ntt(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long batch,
 }
 
 // Pass 1: forward column transforms of a slab of w columns, then the
-// global twiddle.  blockIdx.z selects operand 0 or 1 (src0/src1).
+// global twiddle.  blockIdx.z selects operand 0 or 1 (src0/src1).  Uniform
+// batches read product t at src + t*len; uneven batches (desc != null) at
+// the descriptor's offsets and lengths.
 template <class Ar>
 __global__ void __launch_bounds__(kThreads)
 k_col_fwd(DevPlan<Ar> P, const typename Ar::word* src0, long long len0,
           const typename Ar::word* src1, long long len1, typename Ar::word* dst,
-          long long dst_stride, long long dst_off1, int logN, int k2, int logw, long long prod_base) {
+          long long dst_stride, long long dst_off1, int logN, int k2, int logw, long long prod_base,
+          const BatchDesc* __restrict__ desc) {
     using word = typename Ar::word;
     extern __shared__ __align__(16) unsigned char smraw[];
     word* sm = reinterpret_cast<word*>(smraw);
@@ -167,8 +170,16 @@ k_col_fwd(DevPlan<Ar> P, const typename Ar::word* src0, long long len0,
     const int w = 1 << logw;
     const long long c0 = static_cast<long long>(blockIdx.x) << logw;
     const long long prod = prod_base + blockIdx.y;
-    const word* src = blockIdx.z ? src1 : src0;
-    const long long len = blockIdx.z ? len1 : len0;
+    const word* src;
+    long long len;
+    if (desc) {
+        const BatchDesc d = desc[prod];
+        src = blockIdx.z ? src1 + d.boff : src0 + d.aoff;
+        len = blockIdx.z ? d.nb : d.na;
+    } else {
+        len = blockIdx.z ? len1 : len0;
+        src = (blockIdx.z ? src1 : src0) + prod * len;
+    }
     word* out = dst + prod * dst_stride + (blockIdx.z ? dst_off1 : 0);
     const VecLayout L = slab_layout(k2, logw);
     const long long total = (1LL << k2) << logw;
@@ -176,7 +187,7 @@ k_col_fwd(DevPlan<Ar> P, const typename Ar::word* src0, long long len0,
         const long long row = idx >> logw;
         const int col = static_cast<int>(idx & (w - 1));
         const long long e = row * n1 + c0 + col;
-        sm[vec_addr(L, col, static_cast<int>(row))] = (e < len) ? src[prod * len + e] : word(0);
+        sm[vec_addr(L, col, static_cast<int>(row))] = (e < len) ? src[e] : word(0);
     }
     __syncthreads();
     Hook<Ar> h{P.glob_fwd, static_cast<int>(n1), 0, 1, static_cast<int>(c0)};
@@ -194,7 +205,7 @@ template <class Ar>
 __global__ void __launch_bounds__(kThreads)
 k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
           typename Ar::word* dst, long long out_len, int logN, int k2, int logw,
-          typename Ar::tw scale, long long prod_base) {
+          typename Ar::tw scale, long long prod_base, const BatchDesc* __restrict__ desc) {
     using word = typename Ar::word;
     extern __shared__ __align__(16) unsigned char smraw[];
     word* sm = reinterpret_cast<word*>(smraw);
@@ -204,6 +215,14 @@ k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
     const long long c0 = static_cast<long long>(blockIdx.x) << logw;
     const long long prod = prod_base + blockIdx.y;
     const word* in = src + prod * src_stride;
+    word* outp;
+    if (desc) {
+        const BatchDesc d = desc[prod];
+        outp = dst + d.coff;
+        out_len = static_cast<long long>(d.na) + d.nb - 1;
+    } else {
+        outp = dst + prod * out_len;
+    }
     const VecLayout L = slab_layout(k2, logw);
     const long long total = (1LL << k2) << logw;
     for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
@@ -218,7 +237,7 @@ k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
         const long long row = idx >> logw;
         const int col = static_cast<int>(idx & (w - 1));
         const long long e = row * n1 + c0 + col;
-        if (e < out_len) dst[prod * out_len + e] = P.ar.mulw(sm[vec_addr(L, col, static_cast<int>(row))], scale);
+        if (e < out_len) outp[e] = P.ar.mulw(sm[vec_addr(L, col, static_cast<int>(row))], scale);
     }
 }
 
@@ -291,6 +310,80 @@ k_row_ntt(DevPlan<Ar> P, typename Ar::word* data, int logN, int k2, int lrpc, lo
         const int v = static_cast<int>(idx >> k1);
         const long long i = idx & (n1 - 1);
         base[(r0 + v) * n1 + i] = sm[vec_addr(L, v, static_cast<int>(i))];
+    }
+}
+
+// ------------------------------------------------------------------ uneven batches
+
+// Persistent kernel for the one-block products of an uneven, mixed-modulus
+// batch: every block takes items from a global ticket until none are left;
+// each item is the whole fused product (load with zero padding, two forward
+// transforms, pointwise product, inverse transform, scaled store) for up to
+// 16 products in shared memory.  The modulus constants of the current item
+// are copied into shared memory when the modulus changes.
+template <class Ar>
+__global__ void __launch_bounds__(kThreads)
+k_batch_small(const DevPlan<Ar>* __restrict__ plans, const BatchDesc* __restrict__ desc,
+              const SmallItem<Ar>* __restrict__ items, unsigned nitems, unsigned* ticket,
+              const typename Ar::word* __restrict__ a, const typename Ar::word* __restrict__ b,
+              typename Ar::word* __restrict__ c) {
+    using word = typename Ar::word;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    word* sm = reinterpret_cast<word*>(smraw);
+    __shared__ DevPlan<Ar> P;
+    __shared__ BatchDesc sd[kSmallMaxPerItem];
+    __shared__ unsigned s_item;
+    __shared__ int s_prime;
+    if (threadIdx.x == 0) s_prime = -1;
+    for (;;) {
+        __syncthreads();                       // previous item fully stored
+        if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const unsigned it = s_item;
+        if (it >= nitems) break;
+        const SmallItem<Ar> I = items[it];
+        if (static_cast<int>(I.prime) != s_prime) {
+            const unsigned* src = reinterpret_cast<const unsigned*>(plans + I.prime);
+            unsigned* dst = reinterpret_cast<unsigned*>(&P);
+            for (int i = threadIdx.x; i < static_cast<int>(sizeof(DevPlan<Ar>) / 4); i += blockDim.x)
+                dst[i] = src[i];
+        }
+        if (threadIdx.x < I.count) sd[threadIdx.x] = desc[I.first + threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 0) s_prime = static_cast<int>(I.prime);
+        const int logL = static_cast<int>(I.logL);
+        const int lppc = small_lppc(logL);
+        const int ppc = 1 << lppc;
+        const int L = 1 << logL;
+        const VecLayout LA = tile_layout(logL, lppc + 1);
+        for (int idx = threadIdx.x; idx < (L << lppc); idx += blockDim.x) {
+            const int v = idx >> logL;
+            const int i = idx & (L - 1);
+            word xa = 0, xb = 0;
+            if (v < static_cast<int>(I.count)) {
+                if (i < static_cast<int>(sd[v].na)) xa = a[sd[v].aoff + i];
+                if (i < static_cast<int>(sd[v].nb)) xb = b[sd[v].boff + i];
+            }
+            sm[vec_addr(LA, v, i)] = xa;
+            sm[vec_addr(LA, v + ppc, i)] = xb;
+        }
+        __syncthreads();
+        vec_fwd<Ar>(P, sm, LA, nullptr);
+        for (int idx = threadIdx.x; idx < (L << lppc); idx += blockDim.x) {
+            const int v = idx >> logL;
+            const int i = idx & (L - 1);
+            const int pa = vec_addr(LA, v, i), pb = vec_addr(LA, v + ppc, i);
+            sm[pa] = P.ar.mulmont(sm[pa], sm[pb]);
+        }
+        __syncthreads();
+        const VecLayout LC = tile_layout(logL, lppc);
+        vec_inv<Ar>(P, sm, LC, nullptr);
+        for (int idx = threadIdx.x; idx < (L << lppc); idx += blockDim.x) {
+            const int v = idx >> logL;
+            const int i = idx & (L - 1);
+            if (v < static_cast<int>(I.count) && i < static_cast<int>(sd[v].na + sd[v].nb - 1))
+                c[sd[v].coff + i] = P.ar.mulw(sm[vec_addr(LC, v, i)], I.scale);
+        }
     }
 }
 
@@ -381,17 +474,6 @@ static int grid_for(long long total) {
     return static_cast<int>(std::max(1LL, std::min(blocks, 152LL * 32)));
 }
 
-template <class Ar>
-static int col_logw(int k2) {
-    using word = typename Ar::word;
-    int logw = (sizeof(word) == 4) ? 5 : 4;          // 128-byte row segments
-    const int min_logw = (sizeof(word) == 4) ? 3 : 2; // 32-byte sectors at least
-    while (logw > min_logw &&
-           slab_words(slab_layout(k2, logw)) * (long long)sizeof(word) > 100 * 1024)
-        --logw;
-    return logw;
-}
-
 static int row_lrpc(int k1, int operands) {
     // short rows: enough rows that the lanes of a warp span >= 32 lines
     if (k1 <= kMaxLineLog) return operands == 2 ? 4 : 5;
@@ -416,9 +498,10 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
                          cudaStream_t st) {
     using word = typename Ar::word;
     const int k = static_cast<int>(plan->log2n);
+    const LaunchCfg cfg = launch_cfg(sizeof(word), k, plan->tile_max_log);
     prof_begin_call(st);
     if (k <= plan->tile_max_log) {
-        const int lppc = (k <= kMaxLineLog) ? 4 : 0;
+        const int lppc = cfg.lppc;
         const size_t smem = layout_words(tile_layout(k, lppc + 1)) * sizeof(word);
         if (allow_smem(k_tile_polymul<Ar>, smem) != cudaSuccess) return check_launch("smem attr");
         const long long blocks = (batch + (1LL << lppc) - 1) >> lppc;
@@ -434,9 +517,9 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
     }
     const int k2 = plan->k2, k1 = plan->k1;
     const long long N = 1LL << k;
-    const int logw = col_logw<Ar>(k2);
+    const int logw = cfg.logw;
     const size_t smem_c = slab_words(slab_layout(k2, logw)) * sizeof(word);
-    const int lrpc = row_lrpc(k1, 2);
+    const int lrpc = cfg.lrpc;
     const size_t smem_r = layout_words(tile_layout(k1, lrpc + 1)) * sizeof(word);
     if (allow_smem(k_col_fwd<Ar>, smem_c) != cudaSuccess ||
         allow_smem(k_col_inv<Ar>, smem_c) != cudaSuccess ||
@@ -445,14 +528,15 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
     for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
         dim3 gc(static_cast<unsigned>((1LL << k1) >> logw), nbat, 2);
-        k_col_fwd<Ar><<<gc, kThreads, smem_c, st>>>(dp, a, na, b, nb, ws, 2 * N, N, k, k2, logw, p0);
+        k_col_fwd<Ar><<<gc, kThreads, smem_c, st>>>(dp, a, na, b, nb, ws, 2 * N, N, k, k2, logw, p0,
+                                                    nullptr);
         prof_mark(st, "k_col_fwd");
         dim3 gr(static_cast<unsigned>((1LL << k2) >> lrpc), nbat, 1);
         k_row_polymul<Ar><<<gr, kThreads, smem_r, st>>>(dp, ws, 2 * N, k, k2, lrpc, p0);
         prof_mark(st, "k_row_polymul");
         dim3 gi(static_cast<unsigned>((1LL << k1) >> logw), nbat, 1);
         k_col_inv<Ar><<<gi, kThreads, smem_c, st>>>(dp, ws, 2 * N, c, na + nb - 1, k, k2, logw,
-                                                    scale, p0);
+                                                    scale, p0, nullptr);
         prof_mark(st, "k_col_inv");
     }
     return check_launch("fused polymul passes");
@@ -485,6 +569,61 @@ int launch_polymul_plain(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
 }
 
 template <class Ar>
+int launch_batch_small(const DevPlan<Ar>* d_plans, const BatchDesc* d_desc, const void* d_items,
+                       unsigned nitems, unsigned* d_ticket, const typename Ar::word* a,
+                       const typename Ar::word* b, typename Ar::word* c, size_t smem, int grid,
+                       cudaStream_t st) {
+    if (nitems == 0) return NTT_OK;
+    if (allow_smem(k_batch_small<Ar>, smem) != cudaSuccess) return check_launch("smem attr");
+    k_batch_small<Ar><<<grid, kThreads, smem, st>>>(
+        d_plans, d_desc, static_cast<const SmallItem<Ar>*>(d_items), nitems, d_ticket, a, b, c);
+    prof_mark(st, "k_batch_small");
+    return check_launch("k_batch_small");
+}
+
+// Blocks of the persistent kernel resident per SM at `smem` bytes.
+template <class Ar>
+int batch_small_occupancy(size_t smem) {
+    if (allow_smem(k_batch_small<Ar>, smem) != cudaSuccess) return 1;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_small<Ar>, kThreads, smem) != cudaSuccess)
+        return 1;
+    return occ > 0 ? occ : 1;
+}
+
+template <class Ar>
+int launch_batch_bucket(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
+                        const typename Ar::word* b, typename Ar::word* c, const BatchDesc* d_desc,
+                        long long count, typename Ar::word* ws, typename Ar::tw scale,
+                        cudaStream_t st) {
+    using word = typename Ar::word;
+    const int k = static_cast<int>(plan->log2n);
+    const LaunchCfg cfg = launch_cfg(sizeof(word), k, plan->tile_max_log);
+    const int k2 = plan->k2, k1 = plan->k1;
+    const long long N = 1LL << k;
+    const int logw = cfg.logw, lrpc = cfg.lrpc;
+    const size_t smem_c = slab_words(slab_layout(k2, logw)) * sizeof(word);
+    const size_t smem_r = layout_words(tile_layout(k1, lrpc + 1)) * sizeof(word);
+    if (allow_smem(k_col_fwd<Ar>, smem_c) != cudaSuccess ||
+        allow_smem(k_col_inv<Ar>, smem_c) != cudaSuccess ||
+        allow_smem(k_row_polymul<Ar>, smem_r) != cudaSuccess)
+        return check_launch("smem attr");
+    for (long long p0 = 0; p0 < count; p0 += kMaxGridY) {
+        const unsigned nbat = static_cast<unsigned>(std::min(count - p0, kMaxGridY));
+        dim3 gc(static_cast<unsigned>((1LL << k1) >> logw), nbat, 2);
+        k_col_fwd<Ar><<<gc, kThreads, smem_c, st>>>(dp, a, 0, b, 0, ws, 2 * N, N, k, k2, logw, p0, d_desc);
+        prof_mark(st, "k_col_fwd");
+        dim3 gr(static_cast<unsigned>((1LL << k2) >> lrpc), nbat, 1);
+        k_row_polymul<Ar><<<gr, kThreads, smem_r, st>>>(dp, ws, 2 * N, k, k2, lrpc, p0);
+        prof_mark(st, "k_row_polymul");
+        dim3 gi(static_cast<unsigned>((1LL << k1) >> logw), nbat, 1);
+        k_col_inv<Ar><<<gi, kThreads, smem_c, st>>>(dp, ws, 2 * N, c, 0, k, k2, logw, scale, p0, d_desc);
+        prof_mark(st, "k_col_inv");
+    }
+    return check_launch("batch bucket passes");
+}
+
+template <class Ar>
 int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* data, long long batch,
                bool fwd, typename Ar::tw scale, cudaStream_t st) {
     using word = typename Ar::word;
@@ -502,7 +641,7 @@ int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* d
     }
     const int k2 = plan->k2, k1 = plan->k1;
     const long long N = 1LL << k;
-    const int logw = col_logw<Ar>(k2);
+    const int logw = launch_cfg(sizeof(word), k, plan->tile_max_log).logw;
     const size_t smem_c = slab_words(slab_layout(k2, logw)) * sizeof(word);
     const int lrpc = row_lrpc(k1, 1);
     const size_t smem_r = layout_words(tile_layout(k1, lrpc)) * sizeof(word);
@@ -517,7 +656,7 @@ int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* d
         dim3 gr(static_cast<unsigned>((1LL << k2) >> lrpc), nbat, 1);
         if (fwd) {
             k_col_fwd<Ar><<<gc, kThreads, smem_c, st>>>(dp, data, N, data, N, data, N, 0, k, k2,
-                                                        logw, p0);
+                                                        logw, p0, nullptr);
             prof_mark(st, "k_col_fwd");
             krow<<<gr, kThreads, smem_r, st>>>(dp, data, k, k2, lrpc, p0);
             prof_mark(st, "k_row_ntt_fwd");
@@ -525,7 +664,7 @@ int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* d
             krow<<<gr, kThreads, smem_r, st>>>(dp, data, k, k2, lrpc, p0);
             prof_mark(st, "k_row_ntt_inv");
             k_col_inv<Ar><<<gc, kThreads, smem_c, st>>>(dp, data, N, data, N, k, k2, logw, scale,
-                                                        p0);
+                                                        p0, nullptr);
             prof_mark(st, "k_col_inv");
         }
     }

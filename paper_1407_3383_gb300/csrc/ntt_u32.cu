@@ -9,6 +9,13 @@ template int launch_polymul_fused<Mont32>(const ntt_plan*, const DevPlan<Mont32>
 template int launch_polymul_plain<Mont32>(const ntt_plan*, const DevPlan<Mont32>&, const uint32_t*,
                                           long long, const uint32_t*, long long, long long, uint32_t*,
                                           uint32_t*, Tw32, cudaStream_t);
+template int launch_batch_small<Mont32>(const DevPlan<Mont32>*, const BatchDesc*, const void*, unsigned,
+                                         unsigned*, const uint32_t*, const uint32_t*, uint32_t*, size_t, int,
+                                         cudaStream_t);
+template int launch_batch_bucket<Mont32>(const ntt_plan*, const DevPlan<Mont32>&, const uint32_t*,
+                                          const uint32_t*, uint32_t*, const BatchDesc*, long long,
+                                          uint32_t*, Tw32, cudaStream_t);
+template int batch_small_occupancy<Mont32>(size_t);
 template int launch_ntt<Mont32>(const ntt_plan*, const DevPlan<Mont32>&, uint32_t*, long long, bool,
                                 Tw32, cudaStream_t);
 

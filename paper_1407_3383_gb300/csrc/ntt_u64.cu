@@ -9,6 +9,13 @@ template int launch_polymul_fused<Shoup64>(const ntt_plan*, const DevPlan<Shoup6
 template int launch_polymul_plain<Shoup64>(const ntt_plan*, const DevPlan<Shoup64>&, const uint64_t*,
                                            long long, const uint64_t*, long long, long long,
                                            uint64_t*, uint64_t*, Tw64, cudaStream_t);
+template int launch_batch_small<Shoup64>(const DevPlan<Shoup64>*, const BatchDesc*, const void*, unsigned,
+                                         unsigned*, const uint64_t*, const uint64_t*, uint64_t*, size_t, int,
+                                         cudaStream_t);
+template int launch_batch_bucket<Shoup64>(const ntt_plan*, const DevPlan<Shoup64>&, const uint64_t*,
+                                          const uint64_t*, uint64_t*, const BatchDesc*, long long,
+                                          uint64_t*, Tw64, cudaStream_t);
+template int batch_small_occupancy<Shoup64>(size_t);
 template int launch_ntt<Shoup64>(const ntt_plan*, const DevPlan<Shoup64>&, uint64_t*, long long,
                                  bool, Tw64, cudaStream_t);
 

@@ -277,7 +277,9 @@ static void build_tables(ntt_plan* P, TableBuilder<TwT>& tb, Conv conv,
         std::vector<int> tiles;
         const int k = static_cast<int>(P->log2n);
         if (k <= P->tile_max_log) {
-            if (k > kMaxLineLog) tiles.push_back(k);
+            // every tile size up to n, so one plan serves every shorter
+            // one-block product with this modulus (uneven batches)
+            for (int lt = kMaxLineLog + 1; lt <= k; ++lt) tiles.push_back(lt);
         } else {
             if (P->k2 > kMaxLineLog) tiles.push_back(P->k2);
             if (P->k1 > kMaxLineLog && P->k1 != P->k2) tiles.push_back(P->k1);

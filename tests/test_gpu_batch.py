@@ -1,0 +1,109 @@
+"""GPU parity of uneven, mixed-modulus batches (persistent kernel for the
+one-block sizes, bucketed passes for the long products, CUDA-graph replay)
+with the oracle's schoolbook products; at the full 10,000-product workload,
+sampled coefficients and evaluation fingerprints."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1407_3383_gb300 as G
+from paper_1407_3383_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_batch(primes, a_list, b_list, pidx, mode=G.NTT_BATCH_GRAPH, runs=1):
+    import torch
+    na = [x.size for x in a_list]
+    nb = [x.size for x in b_list]
+    with G.BatchPlan(primes, na, nb, pidx) as bp:
+        wb = bp.word_bytes
+        dt = np.uint32 if wb == 4 else np.uint64
+        a = torch.from_numpy(np.concatenate(a_list).astype(dt)).cuda()
+        b = torch.from_numpy(np.concatenate(b_list).astype(dt)).cuda()
+        c = torch.zeros(bp.c_words, dtype=a.dtype, device="cuda")
+        ws = torch.empty(bp.workspace_size(), dtype=torch.uint8, device="cuda")
+        outs = []
+        for _ in range(runs):
+            c.zero_()
+            bp.run(a, b, c, ws, mode)
+            torch.cuda.synchronize()
+            outs.append(c.cpu().numpy().astype(np.uint64))
+        return [[o[int(bp.c_off[t]):int(bp.c_off[t] + bp.nc[t])] for t in range(len(na))] for o in outs]
+
+
+def _random_batch(primes, count, lo, hi, seed):
+    g = W.SplitMix64(seed)
+    la = g.log_uniform_int(lo, hi, count)
+    lb = np.maximum(1, (la * (0.5 + g.unit(count))).astype(np.int64))
+    pidx = g.choice(len(primes), count)
+    a_list = [g.uniform_mod(primes[i], int(n)) for i, n in zip(pidx, la)]
+    b_list = [g.uniform_mod(primes[i], int(n)) for i, n in zip(pidx, lb)]
+    return a_list, b_list, pidx
+
+
+@pytest.mark.parametrize("mode", [G.NTT_BATCH_DIRECT, G.NTT_BATCH_STREAMS, G.NTT_BATCH_GRAPH])
+def test_uneven_batch_u64_full(mode):
+    primes = [W.P1, W.P2, W.P3]
+    a_list, b_list, pidx = _random_batch(primes, 240, 1, 6000, 41)
+    got = _run_batch(primes, a_list, b_list, pidx, mode, runs=2)
+    want = O.polymul_ragged([primes[i] for i in pidx], a_list, b_list)
+    for r in range(2):                                  # graph capture, then replay
+        for t in range(len(want)):
+            assert (got[r][t] == want[t]).all(), (r, t, a_list[t].size, b_list[t].size)
+
+
+def test_uneven_batch_u32_full():
+    primes = [W.P_A, W.P_B, W.P_TABLE11]
+    a_list, b_list, pidx = _random_batch(primes, 200, 1, 12000, 42)
+    got = _run_batch(primes, a_list, b_list, pidx)[0]
+    want = O.polymul_ragged([primes[i] for i in pidx], a_list, b_list)
+    for t in range(len(want)):
+        assert (got[t] == want[t]).all(), t
+
+
+def test_config3_full_workload_sampled():
+    """10,000 products, lengths log-uniform in [2^6, 2^18], each modulo one
+    of three 62-bit primes: sampled coefficients and fingerprints."""
+    lengths, pidx = W.config3_shapes()
+    primes_used, a_list, b_list = W.config3_operands(lengths, pidx)
+    primes = [W.P1, W.P2, W.P3]
+    got = _run_batch(primes, a_list, b_list, pidx)[0]
+    g = W.SplitMix64(77)
+    picks = list((g.u64(60) % np.uint64(len(a_list))).astype(np.int64))
+    picks += [int(np.argmax(lengths)), int(np.argmin(lengths))]
+    for t in picks:
+        p = primes_used[t]
+        n = a_list[t].size + b_list[t].size - 1
+        for k in [0, n - 1, n // 2] + [int(v) for v in g.u64(3) % np.uint64(n)]:
+            assert int(got[t][k]) == O.poly_coeff(p, a_list[t], b_list[t], k), (t, k)
+        x = int(g.uniform_mod(p, 1)[0])
+        assert O.eval_poly(p, got[t], x) == O.mulmod(O.eval_poly(p, a_list[t], x),
+                                                     O.eval_poly(p, b_list[t], x), p)
+
+
+def test_batch_rejects_bad_descriptors():
+    with pytest.raises(G.NttError):
+        G.BatchPlan([W.P1], [10, 0], [10, 5], [0, 0])           # empty operand
+    with pytest.raises(G.NttError):
+        G.BatchPlan([W.P1, W.P_A], [10], [10], [0])              # mixed word sizes
+    with pytest.raises(G.NttError):
+        G.BatchPlan([W.P1], [10], [10], [3])                     # bad modulus index
+
+
+def test_autotune_keeps_results_exact():
+    import torch
+    p, a, b = W.config1(count=8)
+    with G.Plan(p, 16) as plan:
+        G.ntt_autotune(plan, 8)
+        lppc, logw, lrpc = G.ntt_tune_get(4, 16)
+        assert logw >= 1
+        da = torch.from_numpy(a.reshape(-1)).cuda()
+        db = torch.from_numpy(b.reshape(-1)).cuda()
+        dc = torch.empty(8 * ((1 << 16) - 1), dtype=torch.uint32, device="cuda")
+        ws = G.alloc_workspace(plan, 8)
+        G.polymul_mod_p_batch(plan, da, 1 << 15, db, 1 << 15, 8, dc, G.NTT_SCHED_FUSED, ws)
+        torch.cuda.synchronize()
+        got = dc.cpu().numpy().reshape(8, -1).astype(np.uint64)
+        want = O.polymul_batch(p, a[:1].astype(np.uint64), b[:1].astype(np.uint64))
+        assert (got[:1] == want).all()

@@ -1,0 +1,26 @@
+"""Host side of the launch-shape table (no device work): import/export round
+trip and rejection of shapes that cannot launch."""
+import pytest
+
+import paper_1407_3383_gb300 as G
+
+
+def test_tune_table_round_trip():
+    G.ntt_tune_import("8 20 0 3 1\n4 15 0 4 2\n")
+    assert G.ntt_tune_get(8, 20) == (0, 3, 1)
+    assert G.ntt_tune_get(4, 15) == (0, 4, 2)
+    text = G.ntt_tune_export()
+    assert "8 20 0 3 1" in text and "4 15 0 4 2" in text
+
+
+def test_tune_rejects_bad_shapes():
+    with pytest.raises(G.NttError):
+        G.ntt_tune_import("4 16 0 9 3\n")     # 512 columns per block
+    with pytest.raises(G.NttError):
+        G.ntt_tune_import("5 16 0 4 3\n")     # no 5-byte words
+
+
+def test_default_shapes():
+    # one-block sizes: 16 products per block for short vectors, 1 for tiles
+    assert G.ntt_tune_get(4, 8)[0] == 4
+    assert G.ntt_tune_get(8, 12)[0] == 0
