@@ -225,6 +225,55 @@ size_t polymul_batch_workspace_size(const polymul_batch_plan* plan);
 int polymul_batch_run(polymul_batch_plan* plan, const void* d_a, const void* d_b, void* d_c,
                       void* d_ws, size_t ws_bytes, unsigned mode, void* stream);
 
+/* ---- serving loop ------------------------------------------------------------ */
+
+/* Request kinds and flags for ntt_server_submit. */
+#define NTT_REQ_INTMUL 0u     /* integer product, 32-bit limbs (Section 5.3) */
+#define NTT_REQ_POLYMUL 1u    /* polynomial product over Z/P_iZ, 64-bit words (Section 5.2) */
+#define NTT_REQ_DEVICE 0x1u   /* a, b, c are device buffers: no copies, no operand memory */
+
+typedef struct ntt_server_config {
+    size_t max_limbs;   /* largest operand (limbs, or words for polynomial products) */
+    size_t mem_bytes;   /* device arena for operands, outputs and scratch */
+    unsigned slots;     /* requests in flight at once (one CUDA stream each) */
+    unsigned reserved;
+} ntt_server_config;
+
+typedef struct ntt_server ntt_server;
+
+/* Start a server on the current device: builds the transform tables of the
+ * three 62-bit primes for every length up to max_limbs, allocates the arena
+ * and `slots` streams, and starts the scheduler thread.  (The paper has no
+ * serving loop; its products run one at a time.) */
+int ntt_server_create(const ntt_server_config* cfg, ntt_server** out);
+
+/* Queue a product: c = a * b with a of na and b of nb elements.  For
+ * NTT_REQ_INTMUL, c receives na + nb limbs; for NTT_REQ_POLYMUL, c receives
+ * na + nb - 1 words reduced modulo P_prime (prime in 0..2).  Host buffers
+ * (pinned for asynchronous copies) unless NTT_REQ_DEVICE; they must stay
+ * valid until the request completes.  Requests are admitted in arrival
+ * order when a slot and arena memory are free.  *id_out identifies it.
+ * NTT_ERR_SIZE / NTT_ERR_OOM if it can never fit. */
+int ntt_server_submit(ntt_server* server, unsigned kind, unsigned prime, const void* a, size_t na,
+                      const void* b, size_t nb, void* c, unsigned flags, uint64_t* id_out);
+
+/* *state: 0 pending, 1 running, 2 done, 3 failed; *latency_ms (done or
+ * failed only): submission to completion of the result copy, host clock.
+ * Returns the request's error status once it failed. */
+int ntt_server_poll(ntt_server* server, uint64_t id, int* state, double* latency_ms);
+
+/* Wait up to timeout_ms for the request; NTT_ERR_TIMEOUT if it is not done. */
+int ntt_server_wait(ntt_server* server, uint64_t id, int timeout_ms, double* latency_ms);
+
+/* Forget a finished request. */
+int ntt_server_release(ntt_server* server, uint64_t id);
+
+int ntt_server_stats(ntt_server* server, uint64_t* completed, uint64_t* pending, uint64_t* running,
+                     uint64_t* peak_inflight);
+
+/* Stop the scheduler, wait for work in flight, free everything. */
+int ntt_server_destroy(ntt_server* server);
+
 /* ---- launch-shape autotuning ------------------------------------------------ */
 
 /* Time the candidate launch shapes of the fused product for this plan's

@@ -39,6 +39,9 @@ NTT_MM_SUB = 7
 NTT_BATCH_DIRECT = 0
 NTT_BATCH_STREAMS = 1
 NTT_BATCH_GRAPH = 2
+NTT_REQ_INTMUL = 0
+NTT_REQ_POLYMUL = 1
+NTT_REQ_DEVICE = 0x1
 
 _lock = threading.Lock()
 _lib = None
@@ -105,6 +108,16 @@ def _load():
                                     ctypes.POINTER(_int)]),
             "ntt_tune_export": (_int, [ctypes.c_char_p, _sz, ctypes.POINTER(_sz)]),
             "ntt_tune_import": (_int, [ctypes.c_char_p]),
+            "ntt_server_create": (_int, [_vp, ctypes.POINTER(_vp)]),
+            "ntt_server_submit": (_int, [_vp, _uint, _uint, _vp, _sz, _vp, _sz, _vp, _uint,
+                                         ctypes.POINTER(_u64)]),
+            "ntt_server_poll": (_int, [_vp, _u64, ctypes.POINTER(_int),
+                                       ctypes.POINTER(ctypes.c_double)]),
+            "ntt_server_wait": (_int, [_vp, _u64, _int, ctypes.POINTER(ctypes.c_double)]),
+            "ntt_server_release": (_int, [_vp, _u64]),
+            "ntt_server_stats": (_int, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64),
+                                        ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+            "ntt_server_destroy": (_int, [_vp]),
             "intmul_plan_create": (_int, [_sz, ctypes.POINTER(_vp)]),
             "intmul_plan_destroy": (_int, [_vp]),
             "intmul_workspace_size": (_sz, [_vp, _sz, _sz]),
@@ -313,6 +326,71 @@ class BatchPlan:
         if getattr(self, "handle", None):
             _load().polymul_batch_plan_destroy(self.handle)
             self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+# ---------------------------------------------------------------- serving loop
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_limbs", _sz), ("mem_bytes", _sz), ("slots", _uint), ("reserved", _uint)]
+
+
+class Server:
+    """ntt_server: continuous batching of integer / polynomial products."""
+
+    def __init__(self, max_limbs: int, mem_bytes: int, slots: int = 4):
+        cfg = ServerConfig(max_limbs, mem_bytes, slots, 0)
+        h = _vp()
+        _check(_load().ntt_server_create(ctypes.byref(cfg), ctypes.byref(h)), "ntt_server_create")
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, kind: int, a, b, c, prime: int = 0, flags: int = 0, na=None, nb=None) -> int:
+        """a, b, c: tensors (pinned host, or device with NTT_REQ_DEVICE)."""
+        na = a.numel() if na is None else na
+        nb = b.numel() if nb is None else nb
+        rid = _u64()
+        _check(_load().ntt_server_submit(self.handle, kind, prime, _ptr(a), na, _ptr(b), nb, _ptr(c),
+                                         flags, ctypes.byref(rid)), "ntt_server_submit")
+        self._keep[rid.value] = (a, b, c)
+        return rid.value
+
+    def poll(self, rid: int):
+        st, lat = _int(), ctypes.c_double()
+        _check(_load().ntt_server_poll(self.handle, rid, ctypes.byref(st), ctypes.byref(lat)),
+               "ntt_server_poll")
+        return st.value, lat.value
+
+    def wait(self, rid: int, timeout_ms: int = 60000) -> float:
+        lat = ctypes.c_double()
+        _check(_load().ntt_server_wait(self.handle, rid, timeout_ms, ctypes.byref(lat)), "ntt_server_wait")
+        return lat.value
+
+    def release(self, rid: int):
+        _check(_load().ntt_server_release(self.handle, rid), "ntt_server_release")
+        self._keep.pop(rid, None)
+
+    def stats(self):
+        v = [_u64() for _ in range(4)]
+        _check(_load().ntt_server_stats(self.handle, *[ctypes.byref(x) for x in v]), "ntt_server_stats")
+        return dict(zip(["completed", "pending", "running", "peak_inflight"], [x.value for x in v]))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _load().ntt_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -26,14 +26,6 @@
 
 using u128 = unsigned __int128;
 
-struct intmul_plan {
-    int device = 0;
-    unsigned max_log2n = 0;
-    uint64_t P[3] = {0, 0, 0};
-    ntt_plan* plans[3][25] = {};
-    gbntt::Tw64 inv12{}, inv13{}, inv23{};   // P1^-1 mod P2, P1^-1 mod P3, P2^-1 mod P3
-};
-
 namespace gbntt {
 
 namespace {

@@ -28,6 +28,16 @@ struct ntt_plan {
     gbntt::Tw64 inv_scale64{}, pm_scale64{};   // n^-1 ; n^-1 * 2^64
 };
 
+// Three-prime integer product plan (intmul.cu): the primes, a transform plan
+// per prime and length, and the Garner constants.
+struct intmul_plan {
+    int device = 0;
+    unsigned max_log2n = 0;
+    uint64_t P[3] = {0, 0, 0};
+    ntt_plan* plans[3][25] = {};
+    gbntt::Tw64 inv12{}, inv13{}, inv23{};   // P1^-1 mod P2, P1^-1 mod P3, P2^-1 mod P3
+};
+
 namespace gbntt {
 namespace host {
 
