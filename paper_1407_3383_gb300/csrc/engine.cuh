@@ -51,7 +51,7 @@ struct DevPlan {
     const tw* tile_fwd[17];          // [logT] (9..16): [r*L1 + c] = w_T^(c [r]_l2)
     const tw* tile_inv[17];
     const tw* glob_fwd;              // [j2*n1 + j1] = w_N^(j1 [j2]_k2)
-    const tw* glob_inv;
+    const tw* glob_inv;              // w_N^-(j1 [j2]_k2) * N^-1
     const tw* plain_fwd;             // [e] = w_N^e, e < N/2
     const tw* plain_inv;
 };
@@ -94,11 +94,18 @@ template <> struct RadixLog<16> { static constexpr int v = 4; };
 
 // R-point DIF in registers: natural order in, bit-mirrored order out.
 // Stage with half-span h multiplies the difference by w_{2h}^j = w_16^(8j/h).
-template <class Ar, int R>
+// ZHALF: the upper half of the inputs is known to be zero (zero padding),
+// so the first stage is (u, 0) -> (u, u w) without the sum and difference.
+template <class Ar, int R, bool ZHALF = false>
 __device__ __forceinline__ void dif_regs(const Ar& ar, typename Ar::word (&x)[R],
                                          const typename Ar::tw* rc) {
+    if (ZHALF) {
 #pragma unroll
-    for (int h = R / 2; h >= 1; h >>= 1) {
+        for (int j = 0; j < R / 2; ++j)
+            x[j + R / 2] = (j == 0) ? x[j] : ar.mulw(x[j], rc[(8 / (R / 2)) * j]);
+    }
+#pragma unroll
+    for (int h = ZHALF ? R / 4 : R / 2; h >= 1; h >>= 1) {
 #pragma unroll
         for (int s = 0; s < R; s += 2 * h) {
 #pragma unroll
@@ -146,7 +153,7 @@ struct PhaseGeom {
 // One pass of radix R over every line: sub-transforms of size 2^logM.
 // FWD: DIF then twiddle; inverse: twiddle then DIT.  When M == R this is the
 // innermost level; the hook (if any) applies there.
-template <class Ar, int R, bool FWD>
+template <class Ar, int R, bool FWD, bool ZHALF = false>
 __device__ __forceinline__ void run_pass(const DevPlan<Ar>& P, typename Ar::word* s,
                                          const PhaseGeom& g, int logM,
                                          const Hook<Ar>* hook) {
@@ -174,7 +181,7 @@ __device__ __forceinline__ void run_pass(const DevPlan<Ar>& P, typename Ar::word
         const int st = (1 << logMR) * g.ES;
         word x[R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) x[t] = b[t * st];
+        for (int t = 0; t < (ZHALF ? R / 2 : R); ++t) x[t] = b[t * st];
         if (!FWD) {
             if (ltab) {
 #pragma unroll
@@ -188,7 +195,7 @@ __device__ __forceinline__ void run_pass(const DevPlan<Ar>& P, typename Ar::word
             }
             dit_regs<Ar, R>(P.ar, x, P.rci);
         } else {
-            dif_regs<Ar, R>(P.ar, x, P.rc);
+            dif_regs<Ar, R, ZHALF>(P.ar, x, P.rc);
             if (ltab) {
 #pragma unroll
                 for (int t = 1; t < R; ++t) x[t] = P.ar.mulw(x[t], ltab[j1 * 16 + t]);
@@ -220,10 +227,15 @@ __device__ __forceinline__ void run_pass_r(const DevPlan<Ar>& P, typename Ar::wo
 // All passes of one phase.  Forward: logM = logL, logL-4, ..., the last with
 // radix 2^logM (1..4); the hook applies at that last pass.  Inverse: the
 // same passes in reverse order (hook first).  Ends with __syncthreads().
-template <class Ar>
+template <class Ar, bool ZHALF = false>
 __device__ void phase_fwd(const DevPlan<Ar>& P, typename Ar::word* s, const PhaseGeom& g,
                           const Hook<Ar>* hook) {
     int logM = g.logL;   // >= 1: plans have n >= 2
+    if (ZHALF && logM > 4) {
+        run_pass<Ar, 16, true, true>(P, s, g, logM, nullptr);
+        __syncthreads();
+        logM -= 4;
+    }
     while (logM > 4) {
         run_pass<Ar, 16, true>(P, s, g, logM, nullptr);
         __syncthreads();
@@ -267,19 +279,20 @@ __device__ __forceinline__ int vec_addr(const VecLayout& L, int v, int i) {
 
 // Forward transform of every vector.  vhook (optional) is applied to
 // element `pos` of vector v as tab[pos*A + v*C + off] (its B is ignored).
-template <class Ar>
+// ZHALF: the second half of every vector is zero on input.
+template <class Ar, bool ZHALF = false>
 __device__ void vec_fwd(const DevPlan<Ar>& P, typename Ar::word* s, const VecLayout& L,
                         const Hook<Ar>* vhook) {
     if (L.logL <= kMaxLineLog) {
         PhaseGeom g{L.logL, L.lognvec, 0, L.VS, 0, L.CS, true};
-        phase_fwd<Ar>(P, s, g, vhook);
+        phase_fwd<Ar, ZHALF>(P, s, g, vhook);
         return;
     }
     const int l2 = tile_l2(L.logL), l1 = tile_l1(L.logL);
     // column phase: lines (v, c) of length L2, tile twiddle at its end
     Hook<Ar> th{P.tile_fwd[L.logL], 1 << l1, 1, 0, 0};
     PhaseGeom gc{l2, L.lognvec, l1, L.VS, L.CS, L.RS, L.vfast};
-    phase_fwd<Ar>(P, s, gc, &th);
+    phase_fwd<Ar, ZHALF>(P, s, gc, &th);   // tile rows >= L2/2 hold the zero half
     // row phase: lines (v, r) of length L1; vector position = r*L1 + c
     PhaseGeom gr{l1, L.lognvec, l2, L.VS, L.RS, L.CS, L.vfast};
     if (vhook) {

@@ -155,8 +155,9 @@ k_tile_ntt(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long batch,
 // Pass 1: forward column transforms of a slab of w columns, then the
 // global twiddle.  blockIdx.z selects operand 0 or 1 (src0/src1).  Uniform
 // batches read product t at src + t*len; uneven batches (desc != null) at
-// the descriptor's offsets and lengths.
-template <class Ar>
+// the descriptor's offsets and lengths.  ZHALF: every operand has at most
+// n/2 words, so the upper half of every column is zero padding.
+template <class Ar, bool ZHALF>
 __global__ void __launch_bounds__(kThreads)
 k_col_fwd(DevPlan<Ar> P, const typename Ar::word* src0, long long len0,
           const typename Ar::word* src1, long long len1, typename Ar::word* dst,
@@ -191,7 +192,7 @@ k_col_fwd(DevPlan<Ar> P, const typename Ar::word* src0, long long len0,
     }
     __syncthreads();
     Hook<Ar> h{P.glob_fwd, static_cast<int>(n1), 0, 1, static_cast<int>(c0)};
-    vec_fwd<Ar>(P, sm, L, &h);
+    vec_fwd<Ar, ZHALF>(P, sm, L, &h);        // ZHALF: the upper half of every column is padding
     for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const long long row = idx >> logw;
         const int col = static_cast<int>(idx & (w - 1));
@@ -205,7 +206,8 @@ template <class Ar>
 __global__ void __launch_bounds__(kThreads)
 k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
           typename Ar::word* dst, long long out_len, int logN, int k2, int logw,
-          typename Ar::tw scale, long long prod_base, const BatchDesc* __restrict__ desc) {
+          const typename Ar::tw* __restrict__ itab, long long prod_base,
+          const BatchDesc* __restrict__ desc) {
     using word = typename Ar::word;
     extern __shared__ __align__(16) unsigned char smraw[];
     word* sm = reinterpret_cast<word*>(smraw);
@@ -231,13 +233,14 @@ k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
         sm[vec_addr(L, col, static_cast<int>(row))] = in[row * n1 + c0 + col];
     }
     __syncthreads();
-    Hook<Ar> h{P.glob_inv, static_cast<int>(n1), 0, 1, static_cast<int>(c0)};
+    // itab = inverse step-2 twiddles with the final scaling folded in
+    Hook<Ar> h{itab, static_cast<int>(n1), 0, 1, static_cast<int>(c0)};
     vec_inv<Ar>(P, sm, L, &h);
     for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const long long row = idx >> logw;
         const int col = static_cast<int>(idx & (w - 1));
         const long long e = row * n1 + c0 + col;
-        if (e < out_len) outp[e] = P.ar.mulw(sm[vec_addr(L, col, static_cast<int>(row))], scale);
+        if (e < out_len) outp[e] = sm[vec_addr(L, col, static_cast<int>(row))];
     }
 }
 
@@ -521,22 +524,24 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
     const size_t smem_c = slab_words(slab_layout(k2, logw)) * sizeof(word);
     const int lrpc = cfg.lrpc;
     const size_t smem_r = layout_words(tile_layout(k1, lrpc + 1)) * sizeof(word);
-    if (allow_smem(k_col_fwd<Ar>, smem_c) != cudaSuccess ||
+    const bool zhalf = 2 * std::max(na, nb) <= N;
+    auto kcf = zhalf ? k_col_fwd<Ar, true> : k_col_fwd<Ar, false>;
+    const auto* itab = static_cast<const typename Ar::tw*>(plan->glob_inv_pm);
+    if (allow_smem(kcf, smem_c) != cudaSuccess ||
         allow_smem(k_col_inv<Ar>, smem_c) != cudaSuccess ||
         allow_smem(k_row_polymul<Ar>, smem_r) != cudaSuccess)
         return check_launch("smem attr");
     for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
         dim3 gc(static_cast<unsigned>((1LL << k1) >> logw), nbat, 2);
-        k_col_fwd<Ar><<<gc, kThreads, smem_c, st>>>(dp, a, na, b, nb, ws, 2 * N, N, k, k2, logw, p0,
-                                                    nullptr);
+        kcf<<<gc, kThreads, smem_c, st>>>(dp, a, na, b, nb, ws, 2 * N, N, k, k2, logw, p0, nullptr);
         prof_mark(st, "k_col_fwd");
         dim3 gr(static_cast<unsigned>((1LL << k2) >> lrpc), nbat, 1);
         k_row_polymul<Ar><<<gr, kThreads, smem_r, st>>>(dp, ws, 2 * N, k, k2, lrpc, p0);
         prof_mark(st, "k_row_polymul");
         dim3 gi(static_cast<unsigned>((1LL << k1) >> logw), nbat, 1);
-        k_col_inv<Ar><<<gi, kThreads, smem_c, st>>>(dp, ws, 2 * N, c, na + nb - 1, k, k2, logw,
-                                                    scale, p0, nullptr);
+        k_col_inv<Ar><<<gi, kThreads, smem_c, st>>>(dp, ws, 2 * N, c, na + nb - 1, k, k2, logw, itab,
+                                                    p0, nullptr);
         prof_mark(st, "k_col_inv");
     }
     return check_launch("fused polymul passes");
@@ -604,20 +609,22 @@ int launch_batch_bucket(const ntt_plan* plan, const DevPlan<Ar>& dp, const typen
     const int logw = cfg.logw, lrpc = cfg.lrpc;
     const size_t smem_c = slab_words(slab_layout(k2, logw)) * sizeof(word);
     const size_t smem_r = layout_words(tile_layout(k1, lrpc + 1)) * sizeof(word);
-    if (allow_smem(k_col_fwd<Ar>, smem_c) != cudaSuccess ||
+    const auto* itab = static_cast<const typename Ar::tw*>(plan->glob_inv_pm);
+    if (allow_smem(k_col_fwd<Ar, false>, smem_c) != cudaSuccess ||
         allow_smem(k_col_inv<Ar>, smem_c) != cudaSuccess ||
         allow_smem(k_row_polymul<Ar>, smem_r) != cudaSuccess)
         return check_launch("smem attr");
     for (long long p0 = 0; p0 < count; p0 += kMaxGridY) {
         const unsigned nbat = static_cast<unsigned>(std::min(count - p0, kMaxGridY));
         dim3 gc(static_cast<unsigned>((1LL << k1) >> logw), nbat, 2);
-        k_col_fwd<Ar><<<gc, kThreads, smem_c, st>>>(dp, a, 0, b, 0, ws, 2 * N, N, k, k2, logw, p0, d_desc);
+        k_col_fwd<Ar, false><<<gc, kThreads, smem_c, st>>>(dp, a, 0, b, 0, ws, 2 * N, N, k, k2, logw, p0,
+                                                           d_desc);
         prof_mark(st, "k_col_fwd");
         dim3 gr(static_cast<unsigned>((1LL << k2) >> lrpc), nbat, 1);
         k_row_polymul<Ar><<<gr, kThreads, smem_r, st>>>(dp, ws, 2 * N, k, k2, lrpc, p0);
         prof_mark(st, "k_row_polymul");
         dim3 gi(static_cast<unsigned>((1LL << k1) >> logw), nbat, 1);
-        k_col_inv<Ar><<<gi, kThreads, smem_c, st>>>(dp, ws, 2 * N, c, 0, k, k2, logw, scale, p0, d_desc);
+        k_col_inv<Ar><<<gi, kThreads, smem_c, st>>>(dp, ws, 2 * N, c, 0, k, k2, logw, itab, p0, d_desc);
         prof_mark(st, "k_col_inv");
     }
     return check_launch("batch bucket passes");
@@ -646,7 +653,7 @@ int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* d
     const int lrpc = row_lrpc(k1, 1);
     const size_t smem_r = layout_words(tile_layout(k1, lrpc)) * sizeof(word);
     auto krow = fwd ? k_row_ntt<Ar, true> : k_row_ntt<Ar, false>;
-    if (allow_smem(k_col_fwd<Ar>, smem_c) != cudaSuccess ||
+    if (allow_smem(k_col_fwd<Ar, false>, smem_c) != cudaSuccess ||
         allow_smem(k_col_inv<Ar>, smem_c) != cudaSuccess || allow_smem(krow, smem_r) != cudaSuccess)
         return check_launch("smem attr");
     prof_begin_call(st);
@@ -655,15 +662,15 @@ int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* d
         dim3 gc(static_cast<unsigned>((1LL << k1) >> logw), nbat, 1);
         dim3 gr(static_cast<unsigned>((1LL << k2) >> lrpc), nbat, 1);
         if (fwd) {
-            k_col_fwd<Ar><<<gc, kThreads, smem_c, st>>>(dp, data, N, data, N, data, N, 0, k, k2,
-                                                        logw, p0, nullptr);
+            k_col_fwd<Ar, false><<<gc, kThreads, smem_c, st>>>(dp, data, N, data, N, data, N, 0, k, k2,
+                                                               logw, p0, nullptr);
             prof_mark(st, "k_col_fwd");
             krow<<<gr, kThreads, smem_r, st>>>(dp, data, k, k2, lrpc, p0);
             prof_mark(st, "k_row_ntt_fwd");
         } else {
             krow<<<gr, kThreads, smem_r, st>>>(dp, data, k, k2, lrpc, p0);
             prof_mark(st, "k_row_ntt_inv");
-            k_col_inv<Ar><<<gc, kThreads, smem_c, st>>>(dp, data, N, data, N, k, k2, logw, scale,
+            k_col_inv<Ar><<<gc, kThreads, smem_c, st>>>(dp, data, N, data, N, k, k2, logw, dp.glob_inv,
                                                         p0, nullptr);
             prof_mark(st, "k_col_inv");
         }

@@ -20,6 +20,9 @@ struct ntt_plan {
     int tile_max_log = 0;       // largest n done by one CTA (both operands resident)
     int k2 = 0, k1 = 0;         // n = 2^k2 rows x 2^k1 columns when log2n > tile_max_log
     void* d_tables = nullptr;   // one device allocation holding every table
+    // inverse step-2 twiddles times n^-1 R (products after Montgomery
+    // pointwise steps); passed to the kernels as an argument of its own
+    const void* glob_inv_pm = nullptr;
     size_t table_bytes = 0;
     gbntt::DevPlan<gbntt::Mont32> dp32{};
     gbntt::DevPlan<gbntt::Shoup64> dp64{};

@@ -253,7 +253,7 @@ void fill_outer_table(std::vector<uint64_t>& vals, uint64_t p, uint64_t w, int l
 template <class TwT, class Conv>
 static void build_tables(ntt_plan* P, TableBuilder<TwT>& tb, Conv conv,
                          size_t (&line_off)[2][kMaxLineLog + 1], size_t (&tile_off)[2][17],
-                         size_t (&glob_off)[2], size_t (&plain_off)[2]) {
+                         size_t (&glob_off)[3], size_t (&plain_off)[2], uint64_t pm_factor) {
     const uint64_t p = P->p;
     const uint64_t g = P->g;
     auto root = [&](int logm, bool fwd) {
@@ -265,7 +265,8 @@ static void build_tables(ntt_plan* P, TableBuilder<TwT>& tb, Conv conv,
         const bool fwd = (d == 0);
         for (int lm = 0; lm <= kMaxLineLog; ++lm) line_off[d][lm] = SIZE_MAX;
         for (int lt = 0; lt <= 16; ++lt) tile_off[d][lt] = SIZE_MAX;
-        glob_off[d] = plain_off[d] = SIZE_MAX;
+        plain_off[d] = SIZE_MAX;
+        if (fwd) glob_off[0] = glob_off[1] = glob_off[2] = SIZE_MAX;
         // radix-16 pass tables for sub-transform sizes 2^5 .. 2^8
         for (int lm = 5; lm <= kMaxLineLog && lm <= static_cast<int>(P->v2); ++lm) {
             fill_line_table<Conv>(vals, p, root(lm, fwd), lm, fwd);
@@ -290,12 +291,24 @@ static void build_tables(ntt_plan* P, TableBuilder<TwT>& tb, Conv conv,
             for (size_t i = 0; i < vals.size(); ++i) tb.data[off + i] = conv(vals[i]);
             tile_off[d][lt] = off;
         }
-        // the twiddle between the two global passes (Algorithm 1, step 2)
+        // the twiddle between the two global passes (Algorithm 1, step 2);
+        // the inverse tables carry the final scaling: n^-1 for the inverse
+        // transform, n^-1 R for a product whose pointwise step divided by R
         if (k > P->tile_max_log) {
             fill_outer_table(vals, p, root(k, fwd), P->k2, P->k1);
-            const size_t off = tb.add(vals.size());
-            for (size_t i = 0; i < vals.size(); ++i) tb.data[off + i] = conv(vals[i]);
-            glob_off[d] = off;
+            if (fwd) {
+                const size_t off = tb.add(vals.size());
+                for (size_t i = 0; i < vals.size(); ++i) tb.data[off + i] = conv(vals[i]);
+                glob_off[0] = off;
+            } else {
+                const uint64_t factors[2] = {P->n_inv, mul_mod(P->n_inv, pm_factor, p)};
+                for (int f = 0; f < 2; ++f) {
+                    const size_t off = tb.add(vals.size());
+                    for (size_t i = 0; i < vals.size(); ++i)
+                        tb.data[off + i] = conv(mul_mod(vals[i], factors[f], p));
+                    glob_off[1 + f] = off;
+                }
+            }
         }
         // w_N^e, e < N/2, for the per-stage schedule
         if (P->flags & NTT_FLAG_PLAIN) {
@@ -313,10 +326,10 @@ static void build_tables(ntt_plan* P, TableBuilder<TwT>& tb, Conv conv,
 }
 
 template <class Ar, class TwT, class Conv>
-static int finish_plan(ntt_plan* P, DevPlan<Ar>& dp, Conv conv) {
+static int finish_plan(ntt_plan* P, DevPlan<Ar>& dp, Conv conv, uint64_t pm_factor) {
     TableBuilder<TwT> tb;
-    size_t line_off[2][kMaxLineLog + 1], tile_off[2][17], glob_off[2], plain_off[2];
-    build_tables<TwT>(P, tb, conv, line_off, tile_off, glob_off, plain_off);
+    size_t line_off[2][kMaxLineLog + 1], tile_off[2][17], glob_off[3], plain_off[2];
+    build_tables<TwT>(P, tb, conv, line_off, tile_off, glob_off, plain_off, pm_factor);
     const uint64_t w16 = pow_mod(P->g, (P->p - 1) >> 4, P->p);
     const uint64_t w16i = pow_mod(w16, P->p - 2, P->p);
     for (int e = 0; e < 8; ++e) {
@@ -346,6 +359,7 @@ static int finish_plan(ntt_plan* P, DevPlan<Ar>& dp, Conv conv) {
     }
     dp.glob_fwd = at(glob_off[0]);
     dp.glob_inv = at(glob_off[1]);
+    P->glob_inv_pm = at(glob_off[2]);
     dp.plain_fwd = at(plain_off[0]);
     dp.plain_inv = at(plain_off[1]);
     return NTT_OK;
@@ -385,15 +399,15 @@ extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_p
         const uint32_t pinv = inv_pow2_32(p32);
         P->dp32.ar = Mont32{p32, pinv};
         auto conv = [p32, pinv](uint64_t v) { return tw32_of(v, p32, pinv); };
-        rc = finish_plan<Mont32, Tw32>(P, P->dp32, conv);
+        rc = finish_plan<Mont32, Tw32>(P, P->dp32, conv, (1ull << 32) % p);
         P->inv_scale32 = conv(P->n_inv);
         P->pm_scale32 = conv(mul_mod(P->n_inv, (1ull << 32) % p, p));
     } else {
         const uint64_t pinv = inv_pow2_64(p);
         P->dp64.ar = Shoup64{p, pinv};
         auto conv = [p](uint64_t v) { return tw64_of(v, p); };
-        rc = finish_plan<Shoup64, Tw64>(P, P->dp64, conv);
         const uint64_t r64 = static_cast<uint64_t>((static_cast<u128>(1) << 64) % p);
+        rc = finish_plan<Shoup64, Tw64>(P, P->dp64, conv, r64);
         P->inv_scale64 = conv(P->n_inv);
         P->pm_scale64 = conv(mul_mod(P->n_inv, r64, p));
     }
