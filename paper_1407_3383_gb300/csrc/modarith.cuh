@@ -19,7 +19,10 @@
 //    Every correction is one subtraction with borrow: x - y rem p is
 //    d = x - y (mod 2^32) plus p when x < y.  Addition is Function 4's form
 //    x + y rem p = x - (p - y) (valid for m = n); the Montgomery tails
-//    hi(x w~) - hi(q p) are the same subtraction.
+//    hi(x w~) - hi(q p) are the same subtraction.  Sums and differences get
+//    the borrow as the high word of a 64-bit difference and add p with one
+//    multiply-add (FMA pipe); the tails use a compare and a select, the form
+//    that stays exact when both high products are equal.
 //
 //  * Shoup64 -- p < 2^62 in 64-bit words.  Fixed-multiplicand products use
 //    Function 8 with n = 64 and psi = floor(2^64 w / p) (Proposition 4: the
@@ -43,18 +46,26 @@ struct Mont32 {
     uint32_t p;      // odd modulus < 2^32
     uint32_t pinv;   // p^-1 rem 2^32
 
-    // x - y rem p for x < p, y <= p.
+    // x - y rem p for x < p, y <= p: the high word of the 64-bit difference
+    // is the borrow mask m, and d + p = m (2^32 - p) + d is one multiply-add.
     __device__ __forceinline__ uint32_t sub(uint32_t x, uint32_t y) const {
+        const uint64_t d = static_cast<uint64_t>(x) - y;
+        const uint32_t m = static_cast<uint32_t>(d >> 32);
+        return m * (0u - p) + static_cast<uint32_t>(d);
+    }
+    __device__ __forceinline__ uint32_t add(uint32_t x, uint32_t y) const { return sub(x, p - y); }
+    // The same difference written with a compare and a select; used for the
+    // Montgomery tails, whose operands come straight from high products.
+    __device__ __forceinline__ uint32_t sub_sel(uint32_t x, uint32_t y) const {
         const uint32_t d = x - y;
         return d + ((x < y) ? p : 0u);
     }
-    __device__ __forceinline__ uint32_t add(uint32_t x, uint32_t y) const { return sub(x, p - y); }
     // x * w rem p for any 32-bit x; t = (w 2^32 rem p, (w 2^32 rem p) p^-1 rem 2^32).
     __device__ __forceinline__ uint32_t mulw(uint32_t x, Tw32 t) const {
         const uint32_t q = x * t.c;
         const uint32_t h = __umulhi(x, t.w);   // < p
         const uint32_t l = __umulhi(q, p);     // < p
-        return sub(h, l);
+        return sub_sel(h, l);
     }
     // x * y * 2^-32 rem p for x, y < p.
     __device__ __forceinline__ uint32_t mulmont(uint32_t x, uint32_t y) const {
@@ -62,7 +73,7 @@ struct Mont32 {
         const uint32_t hi = __umulhi(x, y);
         const uint32_t q = lo * pinv;
         const uint32_t l = __umulhi(q, p);
-        return sub(hi, l);
+        return sub_sel(hi, l);
     }
 };
 
