@@ -228,7 +228,7 @@ __device__ __forceinline__ void run_pass_r(const DevPlan<Ar>& P, typename Ar::wo
 // radix 2^logM (1..4); the hook applies at that last pass.  Inverse: the
 // same passes in reverse order (hook first).  Ends with __syncthreads().
 template <class Ar, bool ZHALF = false>
-__device__ void phase_fwd(const DevPlan<Ar>& P, typename Ar::word* s, const PhaseGeom& g,
+__device__ __forceinline__ void phase_fwd(const DevPlan<Ar>& P, typename Ar::word* s, const PhaseGeom& g,
                           const Hook<Ar>* hook) {
     int logM = g.logL;   // >= 1: plans have n >= 2
     if (ZHALF && logM > 4) {
@@ -246,7 +246,7 @@ __device__ void phase_fwd(const DevPlan<Ar>& P, typename Ar::word* s, const Phas
 }
 
 template <class Ar>
-__device__ void phase_inv(const DevPlan<Ar>& P, typename Ar::word* s, const PhaseGeom& g,
+__device__ __forceinline__ void phase_inv(const DevPlan<Ar>& P, typename Ar::word* s, const PhaseGeom& g,
                           const Hook<Ar>* hook) {
     int last = g.logL - 4 * ((g.logL - 1) / 4);   // 1..4
     run_pass_r<Ar, false>(P, s, g, last, last, hook);
@@ -281,7 +281,7 @@ __device__ __forceinline__ int vec_addr(const VecLayout& L, int v, int i) {
 // element `pos` of vector v as tab[pos*A + v*C + off] (its B is ignored).
 // ZHALF: the second half of every vector is zero on input.
 template <class Ar, bool ZHALF = false>
-__device__ void vec_fwd(const DevPlan<Ar>& P, typename Ar::word* s, const VecLayout& L,
+__device__ __forceinline__ void vec_fwd(const DevPlan<Ar>& P, typename Ar::word* s, const VecLayout& L,
                         const Hook<Ar>* vhook) {
     if (L.logL <= kMaxLineLog) {
         PhaseGeom g{L.logL, L.lognvec, 0, L.VS, 0, L.CS, true};
@@ -304,7 +304,7 @@ __device__ void vec_fwd(const DevPlan<Ar>& P, typename Ar::word* s, const VecLay
 }
 
 template <class Ar>
-__device__ void vec_inv(const DevPlan<Ar>& P, typename Ar::word* s, const VecLayout& L,
+__device__ __forceinline__ void vec_inv(const DevPlan<Ar>& P, typename Ar::word* s, const VecLayout& L,
                         const Hook<Ar>* vhook) {
     if (L.logL <= kMaxLineLog) {
         PhaseGeom g{L.logL, L.lognvec, 0, L.VS, 0, L.CS, true};

@@ -157,13 +157,21 @@ k_tile_ntt(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long batch,
 // batches read product t at src + t*len; uneven batches (desc != null) at
 // the descriptor's offsets and lengths.  ZHALF: every operand has at most
 // n/2 words, so the upper half of every column is zero padding.
-template <class Ar, bool ZHALF>
+// KN nonzero: n = 2^KN and the block shape are fixed at compile time (the
+// runtime arguments must agree), so the index arithmetic of every pass
+// folds away.
+template <class Ar, bool ZHALF, int KN = 0, int LOGW = 0>
 __global__ void __launch_bounds__(kThreads)
 k_col_fwd(DevPlan<Ar> P, const typename Ar::word* src0, long long len0,
           const typename Ar::word* src1, long long len1, typename Ar::word* dst,
           long long dst_stride, long long dst_off1, int logN, int k2, int logw, long long prod_base,
           const BatchDesc* __restrict__ desc) {
     using word = typename Ar::word;
+    if (KN) {
+        logN = KN;
+        k2 = KN / 2;
+        logw = LOGW;
+    }
     extern __shared__ __align__(16) unsigned char smraw[];
     word* sm = reinterpret_cast<word*>(smraw);
     const int k1 = logN - k2;
@@ -202,13 +210,18 @@ k_col_fwd(DevPlan<Ar> P, const typename Ar::word* src0, long long len0,
 
 // Pass 3: inverse twiddle and inverse column transforms, scaled, cropped
 // store of the first out_len words of each product.
-template <class Ar>
+template <class Ar, int KN = 0, int LOGW = 0>
 __global__ void __launch_bounds__(kThreads)
 k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
           typename Ar::word* dst, long long out_len, int logN, int k2, int logw,
           const typename Ar::tw* __restrict__ itab, long long prod_base,
           const BatchDesc* __restrict__ desc) {
     using word = typename Ar::word;
+    if (KN) {
+        logN = KN;
+        k2 = KN / 2;
+        logw = LOGW;
+    }
     extern __shared__ __align__(16) unsigned char smraw[];
     word* sm = reinterpret_cast<word*>(smraw);
     const int k1 = logN - k2;
@@ -247,11 +260,16 @@ k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
 // Pass 2 of the product: rows of both transformed operands -> forward row
 // transforms, pointwise product, inverse row transforms of the product.
 // ws per product: [0, n) operand a, [n, 2n) operand b; result over a.
-template <class Ar>
+template <class Ar, int KN = 0, int LRPC = 0>
 __global__ void __launch_bounds__(kThreads)
 k_row_polymul(DevPlan<Ar> P, typename Ar::word* ws, long long ws_stride, int logN, int k2,
               int lrpc, long long prod_base) {
     using word = typename Ar::word;
+    if (KN) {
+        logN = KN;
+        k2 = KN / 2;
+        lrpc = LRPC;
+    }
     extern __shared__ __align__(16) unsigned char smraw[];
     word* sm = reinterpret_cast<word*>(smraw);
     const int k1 = logN - k2;
@@ -526,10 +544,17 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
     const size_t smem_r = layout_words(tile_layout(k1, lrpc + 1)) * sizeof(word);
     const bool zhalf = 2 * std::max(na, nb) <= N;
     auto kcf = zhalf ? k_col_fwd<Ar, true> : k_col_fwd<Ar, false>;
+    auto kci = k_col_inv<Ar>;
+    auto krp = k_row_polymul<Ar>;
+    // compile-time geometry for the shape of the 2^16-point 32-bit products
+    if (sizeof(word) == 4 && k == 16 && logw == 5 && lrpc == 4) {
+        kcf = zhalf ? k_col_fwd<Ar, true, 16, 5> : k_col_fwd<Ar, false, 16, 5>;
+        kci = k_col_inv<Ar, 16, 5>;
+        krp = k_row_polymul<Ar, 16, 4>;
+    }
     const auto* itab = static_cast<const typename Ar::tw*>(plan->glob_inv_pm);
-    if (allow_smem(kcf, smem_c) != cudaSuccess ||
-        allow_smem(k_col_inv<Ar>, smem_c) != cudaSuccess ||
-        allow_smem(k_row_polymul<Ar>, smem_r) != cudaSuccess)
+    if (allow_smem(kcf, smem_c) != cudaSuccess || allow_smem(kci, smem_c) != cudaSuccess ||
+        allow_smem(krp, smem_r) != cudaSuccess)
         return check_launch("smem attr");
     for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
@@ -537,11 +562,10 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
         kcf<<<gc, kThreads, smem_c, st>>>(dp, a, na, b, nb, ws, 2 * N, N, k, k2, logw, p0, nullptr);
         prof_mark(st, "k_col_fwd");
         dim3 gr(static_cast<unsigned>((1LL << k2) >> lrpc), nbat, 1);
-        k_row_polymul<Ar><<<gr, kThreads, smem_r, st>>>(dp, ws, 2 * N, k, k2, lrpc, p0);
+        krp<<<gr, kThreads, smem_r, st>>>(dp, ws, 2 * N, k, k2, lrpc, p0);
         prof_mark(st, "k_row_polymul");
         dim3 gi(static_cast<unsigned>((1LL << k1) >> logw), nbat, 1);
-        k_col_inv<Ar><<<gi, kThreads, smem_c, st>>>(dp, ws, 2 * N, c, na + nb - 1, k, k2, logw, itab,
-                                                    p0, nullptr);
+        kci<<<gi, kThreads, smem_c, st>>>(dp, ws, 2 * N, c, na + nb - 1, k, k2, logw, itab, p0, nullptr);
         prof_mark(st, "k_col_inv");
     }
     return check_launch("fused polymul passes");
