@@ -52,7 +52,7 @@ static int ntt_dir(const ntt_plan* P, void* d_data, size_t batch, void* stream, 
     if (P->word_bytes == 4)
         return launch_ntt<Mont32>(P, P->dp32, static_cast<uint32_t*>(d_data),
                                   static_cast<long long>(batch), fwd, P->inv_scale32, st);
-    return launch_ntt<Shoup64>(P, P->dp64, static_cast<uint64_t*>(d_data),
+    return launch_ntt<Shoup64L>(P, P->dp64, static_cast<uint64_t*>(d_data),
                                static_cast<long long>(batch), fwd, P->inv_scale64, st);
 }
 
@@ -115,8 +115,8 @@ extern "C" int polymul_mod_p_batch(const ntt_plan* plan, const void* d_a, size_t
     auto c = static_cast<uint64_t*>(d_c);
     auto w = static_cast<uint64_t*>(d_ws);
     return schedule == NTT_SCHED_FUSED
-               ? launch_polymul_fused<Shoup64>(P, P->dp64, a, lna, b, lnb, lb, c, w, P->pm_scale64, st)
-               : launch_polymul_plain<Shoup64>(P, P->dp64, a, lna, b, lnb, lb, c, w, P->pm_scale64, st);
+               ? launch_polymul_fused<Shoup64L>(P, P->dp64, a, lna, b, lnb, lb, c, w, P->pm_scale64, st)
+               : launch_polymul_plain<Shoup64L>(P, P->dp64, a, lna, b, lnb, lb, c, w, P->pm_scale64, st);
 }
 
 extern "C" int polymul_mod_p(const ntt_plan* plan, const void* d_a, size_t na, const void* d_b,

@@ -269,7 +269,7 @@ int enqueue(polymul_batch_plan* B, const void* a, const void* b, void* c, void* 
 int enqueue_any(polymul_batch_plan* B, const void* a, const void* b, void* c, void* ws, cudaStream_t st,
                 bool spread) {
     return B->wb == 4 ? enqueue<Mont32>(B, a, b, c, ws, st, spread)
-                      : enqueue<Shoup64>(B, a, b, c, ws, st, spread);
+                      : enqueue<Shoup64L>(B, a, b, c, ws, st, spread);
 }
 
 void destroy_graph(polymul_batch_plan* B) {
@@ -311,7 +311,7 @@ extern "C" int polymul_batch_plan_create(const uint64_t* primes, unsigned nprime
             return host::tw32_of(v, static_cast<uint32_t>(p), host::inv_pow2_32(static_cast<uint32_t>(p)));
         });
     else
-        rc = plan_products<Shoup64>(B, h_desc, count, [](uint64_t v, uint64_t p) { return host::tw64_of(v, p); });
+        rc = plan_products<Shoup64L>(B, h_desc, count, [](uint64_t v, uint64_t p) { return host::tw64_of(v, p); });
     if (rc == NTT_OK) {
         for (int i = 0; i < kBatchStreams; ++i)
             if (cudaStreamCreateWithFlags(&B->streams[i], cudaStreamNonBlocking) != cudaSuccess ||

@@ -113,8 +113,7 @@ __device__ __forceinline__ void dif_regs(const Ar& ar, typename Ar::word (&x)[R]
                 auto u = x[s + j];
                 auto v = x[s + j + h];
                 x[s + j] = ar.add(u, v);
-                auto d = ar.sub(u, v);
-                x[s + j + h] = (j == 0) ? d : ar.mulw(d, rc[(8 / h) * j]);
+                x[s + j + h] = (j == 0) ? ar.sub(u, v) : ar.mulw(ar.sub_lazy(u, v), rc[(8 / h) * j]);
             }
         }
     }

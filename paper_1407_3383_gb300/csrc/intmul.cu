@@ -334,7 +334,7 @@ extern "C" int intmul_crt(const intmul_plan* plan, const uint32_t* d_a, size_t n
     prof_mark(st, "k_split");
     for (int i = 0; i < 3; ++i) {
         const ntt_plan* np = plan->plans[i][L.log2n];
-        int rc = launch_polymul_fused<Shoup64>(np, np->dp64, red + i * red_stride, L.da,
+        int rc = launch_polymul_fused<Shoup64L>(np, np->dp64, red + i * red_stride, L.da,
                                                red + i * red_stride + L.da, L.db, 1, res + i * L.nc,
                                                poly, np->pm_scale64, st);
         if (rc != NTT_OK) return rc;

@@ -54,6 +54,10 @@ struct Mont32 {
         return m * (0u - p) + static_cast<uint32_t>(d);
     }
     __device__ __forceinline__ uint32_t add(uint32_t x, uint32_t y) const { return sub(x, p - y); }
+    // a difference that only feeds a twiddle product (any 32-bit input)
+    __device__ __forceinline__ uint32_t sub_lazy(uint32_t x, uint32_t y) const { return sub(x, y); }
+    // values are always fully reduced with this policy
+    __device__ __forceinline__ uint32_t canon(uint32_t x) const { return x; }
     // The same difference written with a compare and a select; used for the
     // Montgomery tails, whose operands come straight from high products.
     __device__ __forceinline__ uint32_t sub_sel(uint32_t x, uint32_t y) const {
@@ -107,6 +111,44 @@ struct Shoup64 {
         uint64_t r = hi - l;
         return (hi >= l) ? r : r + p;
     }
+};
+
+// Shoup64L -- the transform kernels' 64-bit policy: lazy residues in
+// [0, 2p) (4p < 2^64 for p < 2^62).  The twiddle product is Function 8
+// without its final test: x w - c p lies in [0, 2p) for every 64-bit x
+// (Proposition 4: the quotient estimate is at most one short).  Sums and
+// differences are taken modulo 2p with one test, except differences that
+// feed a twiddle product, which skip it (x + 2p - y < 4p).  The general
+// (pointwise) product is Montgomery's with m = 64 (x y < 4 p^2 < 2^64 p)
+// and is fully reduced.  canon() brings a lazy value into [0, p) before it
+// leaves a kernel.
+struct Shoup64L {
+    using word = uint64_t;
+    using tw = Tw64;
+    static constexpr int kBits = 64;
+    uint64_t p;      // modulus < 2^62
+    uint64_t pinv;   // p^-1 rem 2^64
+
+    __device__ __forceinline__ uint64_t red2(uint64_t s) const {   // s < 4p -> [0, 2p)
+        const uint64_t t = s - 2 * p;
+        return (s >= 2 * p) ? t : s;
+    }
+    __device__ __forceinline__ uint64_t add(uint64_t x, uint64_t y) const { return red2(x + y); }
+    __device__ __forceinline__ uint64_t sub(uint64_t x, uint64_t y) const { return red2(x + 2 * p - y); }
+    __device__ __forceinline__ uint64_t sub_lazy(uint64_t x, uint64_t y) const { return x + 2 * p - y; }
+    __device__ __forceinline__ uint64_t mulw(uint64_t x, Tw64 t) const {
+        const uint64_t c = __umul64hi(x, t.c);
+        return x * t.w - c * p;
+    }
+    __device__ __forceinline__ uint64_t mulmont(uint64_t x, uint64_t y) const {
+        const uint64_t lo = x * y;
+        const uint64_t hi = __umul64hi(x, y);
+        const uint64_t q = lo * pinv;
+        const uint64_t l = __umul64hi(q, p);
+        const uint64_t r = hi - l;
+        return (hi >= l) ? r : r + p;
+    }
+    __device__ __forceinline__ uint64_t canon(uint64_t x) const { return (x >= p) ? x - p : x; }
 };
 
 }  // namespace gbntt

@@ -166,9 +166,9 @@ __global__ void k_modmul_vec(MMArgs A, const uint64_t* __restrict__ x, const uin
                 case NTT_MM_BARRETT:
                     r = barrett64(static_cast<u128>(xi) * yi, p, A.bar);
                     break;
-                case NTT_MM_SHOUP: {
-                    const Shoup64 ar{p, A.pinv};
-                    r = ar.mulw(xi, Tw64{yi, yc[i]});
+                case NTT_MM_SHOUP: {   // the 64-bit kernels' lazy twiddle product, then canon
+                    const Shoup64L ar{p, A.pinv};
+                    r = ar.canon(ar.mulw(xi, Tw64{yi, yc[i]}));
                     break;
                 }
                 case NTT_MM_MONTGOMERY: {
@@ -179,16 +179,20 @@ __global__ void k_modmul_vec(MMArgs A, const uint64_t* __restrict__ x, const uin
                     break;
                 }
                 case NTT_MM_MONT_PRODUCT: {
-                    const Shoup64 ar{p, A.pinv};
+                    const Shoup64L ar{p, A.pinv};
                     r = ar.mulmont(ar.mulmont(xi, yi), A.r2);
                     break;
                 }
-                case NTT_MM_ADD:
-                    r = Shoup64{p, A.pinv}.add(xi, yi);
+                case NTT_MM_ADD: {
+                    const Shoup64L ar{p, A.pinv};
+                    r = ar.canon(ar.add(xi, yi));
                     break;
-                case NTT_MM_SUB:
-                    r = Shoup64{p, A.pinv}.sub(xi, yi);
+                }
+                case NTT_MM_SUB: {
+                    const Shoup64L ar{p, A.pinv};
+                    r = ar.canon(ar.sub(xi, yi));
                     break;
+                }
                 default:
                     r = fma_mulmod(static_cast<double>(xi), static_cast<double>(yi), A.dp, A.u);
             }

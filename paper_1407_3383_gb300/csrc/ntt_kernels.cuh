@@ -116,7 +116,7 @@ k_tile_polymul(DevPlan<Ar> P, const typename Ar::word* __restrict__ a, long long
         const int v = static_cast<int>(idx / nc);
         const long long i = idx - v * nc;
         const long long prod = prod0 + v;
-        if (prod < batch) c[prod * nc + i] = P.ar.mulw(sm[vec_addr(LC, v, static_cast<int>(i))], scale);
+        if (prod < batch) c[prod * nc + i] = P.ar.canon(P.ar.mulw(sm[vec_addr(LC, v, static_cast<int>(i))], scale));
     }
 }
 
@@ -147,7 +147,7 @@ k_tile_ntt(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long batch,
         const long long prod = prod0 + v;
         if (prod < batch) {
             word x = sm[vec_addr(LA, v, static_cast<int>(i))];
-            data[prod * L + i] = FWD ? x : P.ar.mulw(x, scale);
+            data[prod * L + i] = P.ar.canon(FWD ? x : P.ar.mulw(x, scale));
         }
     }
 }
@@ -253,7 +253,7 @@ k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
         const long long row = idx >> logw;
         const int col = static_cast<int>(idx & (w - 1));
         const long long e = row * n1 + c0 + col;
-        if (e < out_len) outp[e] = sm[vec_addr(L, col, static_cast<int>(row))];
+        if (e < out_len) outp[e] = P.ar.canon(sm[vec_addr(L, col, static_cast<int>(row))]);
     }
 }
 
@@ -330,7 +330,7 @@ k_row_ntt(DevPlan<Ar> P, typename Ar::word* data, int logN, int k2, int lrpc, lo
     for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const int v = static_cast<int>(idx >> k1);
         const long long i = idx & (n1 - 1);
-        base[(r0 + v) * n1 + i] = sm[vec_addr(L, v, static_cast<int>(i))];
+        base[(r0 + v) * n1 + i] = P.ar.canon(sm[vec_addr(L, v, static_cast<int>(i))]);
     }
 }
 
@@ -403,7 +403,7 @@ k_batch_small(const DevPlan<Ar>* __restrict__ plans, const BatchDesc* __restrict
             const int v = idx >> logL;
             const int i = idx & (L - 1);
             if (v < static_cast<int>(I.count) && i < static_cast<int>(sd[v].na + sd[v].nb - 1))
-                c[sd[v].coff + i] = P.ar.mulw(sm[vec_addr(LC, v, i)], I.scale);
+                c[sd[v].coff + i] = P.ar.canon(P.ar.mulw(sm[vec_addr(LC, v, i)], I.scale));
         }
     }
 }
@@ -477,7 +477,7 @@ __global__ void k_plain_store(DevPlan<Ar> P, const typename Ar::word* ws, typena
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const long long arr = idx / nc, i = idx - arr * nc;
-        c[idx] = P.ar.mulw(ws[(arr << logN) + i], scale);
+        c[idx] = P.ar.canon(P.ar.mulw(ws[(arr << logN) + i], scale));
     }
 }
 

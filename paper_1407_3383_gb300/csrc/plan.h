@@ -25,7 +25,7 @@ struct ntt_plan {
     const void* glob_inv_pm = nullptr;
     size_t table_bytes = 0;
     gbntt::DevPlan<gbntt::Mont32> dp32{};
-    gbntt::DevPlan<gbntt::Shoup64> dp64{};
+    gbntt::DevPlan<gbntt::Shoup64L> dp64{};
     // scaling constants, already in the policy's multiplicand form
     gbntt::Tw32 inv_scale32{}, pm_scale32{};   // n^-1 ; n^-1 * 2^32 (after Montgomery products)
     gbntt::Tw64 inv_scale64{}, pm_scale64{};   // n^-1 ; n^-1 * 2^64

@@ -404,10 +404,10 @@ extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_p
         P->pm_scale32 = conv(mul_mod(P->n_inv, (1ull << 32) % p, p));
     } else {
         const uint64_t pinv = inv_pow2_64(p);
-        P->dp64.ar = Shoup64{p, pinv};
+        P->dp64.ar = Shoup64L{p, pinv};
         auto conv = [p](uint64_t v) { return tw64_of(v, p); };
         const uint64_t r64 = static_cast<uint64_t>((static_cast<u128>(1) << 64) % p);
-        rc = finish_plan<Shoup64, Tw64>(P, P->dp64, conv, r64);
+        rc = finish_plan<Shoup64L, Tw64>(P, P->dp64, conv, r64);
         P->inv_scale64 = conv(P->n_inv);
         P->pm_scale64 = conv(mul_mod(P->n_inv, r64, p));
     }
