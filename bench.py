@@ -57,6 +57,8 @@ def parse():
                     help="polymul: the batched product (headline); serve: the Poisson "
                          "stream of integer products through the serving loop")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per stream")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shape (profiler captures)")
     return ap.parse_args()
 
 
@@ -202,13 +204,16 @@ def make_inputs():
     return p, a, b
 
 
+KERNEL_SOURCES = ["engine.cuh", "modarith.cuh", "ntt_kernels.cuh", "ntt_u32.cu", "ntt_u64.cu"]
+
+
 def source_hash() -> str:
+    """Hash of the sources that define the transform/product kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1407_3383_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(name.encode())
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for name in KERNEL_SOURCES:
+        h.update(name.encode())
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -350,7 +355,7 @@ def run_native(args, world, rank, local):
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
     # the project's autotuner picks the launch shape for this (word size, n)
     # before anything is timed
-    tuned_ms = G.ntt_autotune(plan, batch, stream=stream)
+    tuned_ms = None if args.no_autotune else G.ntt_autotune(plan, batch, stream=stream)
     shape = dict(zip(["log2_products_per_block", "log2_columns_per_block", "log2_rows_per_block"],
                      G.ntt_tune_get(plan.word_bytes, log2n)))
 
