@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None, choices=["fused"],
                     help="run only the fused timed steps (for profiler captures)")
-    ap.add_argument("--workload", default="polymul", choices=["polymul", "serve"],
+    ap.add_argument("--workload", default="polymul", choices=["polymul", "serve", "modmul"],
                     help="polymul: the batched product (headline); serve: the Poisson "
                          "stream of integer products through the serving loop")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per stream")
@@ -558,10 +558,39 @@ def run_serve(args, world, rank, local):
         }), flush=True)
 
 
+def run_modmul(args, world, rank, local):
+    """Throughput of each modular-product variant (Functions 6, 8, 13, 16 and
+    the kernels' Remark 8 form) on register-resident operands: the
+    floating-point-quotient ablation against the integer reductions."""
+    import paper_1407_3383_gb300 as G
+    from paper_1407_3383_gb300 import workloads as W
+    import torch
+    torch.cuda.set_device(local)
+    names = {G.NTT_MM_BARRETT: "barrett_f6", G.NTT_MM_SHOUP: "shoup_f8",
+             G.NTT_MM_MONTGOMERY: "montgomery_f13", G.NTT_MM_FMA: "fp64_fma_f16",
+             G.NTT_MM_MONT_FIXED: "montgomery_fixed_remark8"}
+    cases = [(W.P_TABLE11, 4, "469762049 (29-bit, u32)"), (W.P_B, 4, "3*2^30+1 (32-bit, u32)"),
+             (W.P_TABLE12, 8, "1108307720798209 (50-bit, u64)"), (W.P1, 8, "P1 (62-bit, u64)")]
+    res = {}
+    for p, wb, label in cases:
+        row = {}
+        for kind, nm in names.items():
+            try:
+                row[nm] = G.ntt_modmul_rate(p, kind, wb, 2048) / 1e9
+            except G.NttError:
+                row[nm] = None
+        res[label] = row
+    if rank == 0:
+        print(json.dumps({"metric": "modular products per second by reduction (G/s), register-resident",
+                          "unit": "Gmulmod/s", "results": res, "n_gpus": world}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
-    if args.workload == "serve" and args.impl == "native":
+    if args.workload == "modmul" and args.impl == "native":
+        run_modmul(args, world, rank, local)
+    elif args.workload == "serve" and args.impl == "native":
         run_serve(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)

@@ -180,6 +180,20 @@ int polymul_mod_p_batch_static(const ntt_plan* plan, const void* d_a, size_t na,
                                const void* d_b, size_t nb, size_t batch, void* d_c,
                                void* stream);
 
+/* ---- polynomial matrix products (Section 5.2) ---------------------------- */
+
+/* Workspace bytes for polymat_mul with this plan and n x n matrices. */
+size_t polymat_workspace_size(const ntt_plan* plan, unsigned n);
+
+/* C = A B for n x n matrices of polynomials over Z/pZ of degree < d:
+ * transforms of length 2^log2n of every entry, an n x n matrix product over
+ * F_p at every frequency, inverse transforms of the n^2 entries of C
+ * (Section 5.2, the polynomial matrix product).  A, B: entry (i, j) at word
+ * (i n + j) d, d words each; C: entry (i, j) at (i n + j)(2d - 1).  Needs
+ * 2d - 1 <= 2^log2n and 1 <= n <= 1024.  Workspace: polymat_workspace_size. */
+int polymat_mul(const ntt_plan* plan, const void* d_A, const void* d_B, unsigned n, size_t d,
+                void* d_C, void* d_ws, size_t ws_bytes, void* stream);
+
 /* ---- uneven batches with mixed moduli ------------------------------------ */
 
 /* One product of an uneven batch: operands a[a_off .. a_off+na) and
@@ -329,6 +343,14 @@ int intmul_crt(const intmul_plan* plan, const uint32_t* d_a, size_t na, const ui
 int ntt_modmul_vec(uint64_t p, unsigned kind, unsigned word_bytes, const uint64_t* d_x,
                    const uint64_t* d_y, const uint64_t* d_yc, uint64_t* d_z, size_t n,
                    void* stream);
+
+/* Throughput of one reduction variant (kinds NTT_MM_BARRETT .. NTT_MM_MONT_FIXED)
+ * on register-resident operands: every GPU thread runs 4 independent chains
+ * of `iters` dependent products x <- x y rem p by a fixed y.  Writes modular
+ * products per second; synchronous; allocates a small buffer.  This is the
+ * measurement behind Sections 2-3's comparison of reductions, taken on the
+ * GPU (Tables 5-8 and 10 time them on one CPU core). */
+int ntt_modmul_rate(uint64_t p, unsigned kind, unsigned word_bytes, int iters, double* products_per_s);
 
 /* ---- diagnostics --------------------------------------------------------- */
 

@@ -80,6 +80,7 @@ def _load():
             "orc_polymul_ragged": (None, [_p64, _p64, _p64, _p64, _p64, _p64, _p64,
                                           _p64, _p64, _sz]),
             "orc_intmul": (None, [_p32, _sz, _p32, _sz, _p32]),
+            "orc_polymat_mul": (None, [_u64, _p64, _p64, _sz, _sz, _p64]),
             "orc_mulmod_vec": (None, [_u64, _p64, _p64, _sz, _p64]),
             "orc_num_threads": (ctypes.c_int, []),
         }
@@ -238,6 +239,17 @@ def polymul_ragged(ps, a_list, b_list) -> list[np.ndarray]:
                                _ptr64(b), _ptr64(boff), _ptr64(nb), _ptr64(c),
                                _ptr64(coff), count)
     return [c[int(coff[t]):int(coff[t] + nc[t])] for t in range(count)]
+
+
+def polymat_mul(p: int, A, B) -> np.ndarray:
+    """A, B: (n, n, d) -> C: (n, n, 2d-1), C_ij = sum_l A_il B_lj over Z/pZ."""
+    A = _u64arr(A)
+    B = _u64arr(B)
+    n, n2, d = A.shape
+    assert n == n2 and B.shape == A.shape
+    C = np.empty((n, n, 2 * d - 1), dtype=np.uint64)
+    _load().orc_polymat_mul(p, _ptr64(A), _ptr64(B), n, d, _ptr64(C))
+    return C
 
 
 def intmul(a, b) -> np.ndarray:

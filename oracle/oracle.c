@@ -246,6 +246,27 @@ void orc_polymul_ragged(const uint64_t* ps, const uint64_t* a, const uint64_t* a
         orc_polymul(ps[t], a + aoff[t], na[t], b + boff[t], nb[t], c + coff[t]);
 }
 
+/* Product of two n x n matrices of polynomials over Z/pZ (Section 5.2's
+ * polynomial matrix product), straight from the definition:
+ * C_ij = sum_l A_il B_lj, each A_il B_lj a schoolbook polynomial product.
+ * A, B: entry (i, j) at ((i n + j) d ...), d coefficients each; C: entry
+ * (i, j) at ((i n + j)(2d - 1) ...).  OpenMP over the entries of C. */
+void orc_polymat_mul(uint64_t p, const uint64_t* A, const uint64_t* B, size_t n, size_t d, uint64_t* C) {
+    const size_t dc = 2 * d - 1;
+    long long e;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (e = 0; e < (long long)(n * n); e++) {
+        const size_t i = (size_t)e / n, j = (size_t)e % n;
+        uint64_t* c = C + (size_t)e * dc;
+        for (size_t k = 0; k < dc; k++) c[k] = 0;
+        for (size_t l = 0; l < n; l++) {
+            const uint64_t* a = A + (i * n + l) * d;
+            const uint64_t* b = B + (l * n + j) * d;
+            for (size_t k = 0; k < dc; k++) c[k] = orc_addmod(c[k], orc_poly_coeff(p, a, d, b, d, k), p);
+        }
+    }
+}
+
 /* Schoolbook product of two non-negative integers given as little-endian
  * 32-bit limbs (Section 5.3 multiplies integers a, b of at most N bits).
  * c has na + nb limbs. */

@@ -99,6 +99,9 @@ def _load():
             "polymul_mod_p": (_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp]),
             "polymul_mod_p_batch_static": (_int, [_vp, _vp, _sz, _vp, _sz, _sz, _vp, _vp]),
             "ntt_modmul_vec": (_int, [_u64, _uint, _uint, _vp, _vp, _vp, _vp, _sz, _vp]),
+            "ntt_modmul_rate": (_int, [_u64, _uint, _uint, _int, ctypes.POINTER(ctypes.c_double)]),
+            "polymat_workspace_size": (_sz, [_vp, _uint]),
+            "polymat_mul": (_int, [_vp, _vp, _vp, _uint, _sz, _vp, _vp, _sz, _vp]),
             "polymul_batch_plan_create": (_int, [_vp, _uint, _vp, _sz, _uint, ctypes.POINTER(_vp)]),
             "polymul_batch_plan_destroy": (_int, [_vp]),
             "polymul_batch_workspace_size": (_sz, [_vp]),
@@ -274,6 +277,18 @@ def ntt_modmul_vec(p: int, kind: int, word_bytes: int, x, y, yc, z, n: int | Non
     n = x.numel() if n is None else n
     _check(_load().ntt_modmul_vec(p, kind, word_bytes, _ptr(x), _ptr(y), _ptr(yc), _ptr(z), n,
                                   _stream(stream)), "ntt_modmul_vec")
+
+
+# ---------------------------------------------------------------- polynomial matrices
+
+def polymat_workspace_size(plan: Plan, n: int) -> int:
+    return int(_load().polymat_workspace_size(plan.handle, n))
+
+
+def polymat_mul(plan: Plan, A, B, n: int, d: int, C, ws, stream=None):
+    ws_bytes = ws.numel() * ws.element_size()
+    _check(_load().polymat_mul(plan.handle, _ptr(A), _ptr(B), n, d, _ptr(C), _ptr(ws), ws_bytes,
+                               _stream(stream)), "polymat_mul")
 
 
 # ---------------------------------------------------------------- uneven batches
@@ -475,6 +490,12 @@ def intmul_crt(plan: IntmulPlan, a, na: int, b, nb: int, c, ws, ws_bytes: int | 
         ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
     _check(_load().intmul_crt(plan.handle, _ptr(a), na, _ptr(b), nb, _ptr(c), _ptr(ws), ws_bytes,
                               _stream(stream)), "intmul_crt")
+
+
+def ntt_modmul_rate(p: int, kind: int, word_bytes: int, iters: int = 2048) -> float:
+    out = ctypes.c_double()
+    _check(_load().ntt_modmul_rate(p, kind, word_bytes, iters, ctypes.byref(out)), "ntt_modmul_rate")
+    return out.value
 
 
 # ---------------------------------------------------------------- conveniences

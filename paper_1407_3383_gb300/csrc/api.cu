@@ -129,3 +129,37 @@ extern "C" int ntt_modmul_vec(uint64_t p, unsigned kind, unsigned word_bytes, co
                               void* stream) {
     return launch_modmul_vec(p, kind, word_bytes, d_x, d_y, d_yc, d_z, n, as_stream(stream));
 }
+
+extern "C" int ntt_modmul_rate(uint64_t p, unsigned kind, unsigned word_bytes, int iters, double* products_per_s) {
+    return modmul_rate(p, kind, word_bytes, iters, products_per_s);
+}
+
+extern "C" size_t polymat_workspace_size(const ntt_plan* plan, unsigned n) {
+    if (!plan || n == 0) return 0;
+    return 3ull * n * n * (size_t(1) << plan->log2n) * plan->word_bytes;
+}
+
+extern "C" int polymat_mul(const ntt_plan* plan, const void* d_A, const void* d_B, unsigned n, size_t d,
+                           void* d_C, void* d_ws, size_t ws_bytes, void* stream) {
+    if (!plan || !d_A || !d_B || !d_C || n == 0 || n > 1024 || d == 0) return NTT_ERR_ARG;
+    if (2 * d - 1 > (size_t(1) << plan->log2n)) {
+        gbntt_set_error("polymat_mul: 2d - 1 exceeds the plan's n");
+        return NTT_ERR_SIZE;
+    }
+    const size_t need = polymat_workspace_size(plan, n);
+    if (!d_ws || ws_bytes < need || !aligned(d_ws, 256)) {
+        gbntt_set_error("polymat_mul: workspace of " + std::to_string(need) + " bytes required");
+        return NTT_ERR_WORKSPACE;
+    }
+    const cudaStream_t st = as_stream(stream);
+    const long long ld = static_cast<long long>(d);
+    if (plan->word_bytes == 4)
+        return launch_polymat<Mont32>(plan, plan->dp32, static_cast<const uint32_t*>(d_A),
+                                      static_cast<const uint32_t*>(d_B), static_cast<int>(n), ld,
+                                      static_cast<uint32_t*>(d_C), static_cast<uint32_t*>(d_ws),
+                                      plan->inv_scale32, plan->r32, st);
+    return launch_polymat<Shoup64L>(plan, plan->dp64, static_cast<const uint64_t*>(d_A),
+                                    static_cast<const uint64_t*>(d_B), static_cast<int>(n), ld,
+                                    static_cast<uint64_t*>(d_C), static_cast<uint64_t*>(d_ws),
+                                    plan->inv_scale64, plan->r64, st);
+}

@@ -43,6 +43,11 @@ int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* d
 
 size_t polymul_ws_bytes(const ntt_plan* plan, size_t batch, unsigned schedule);
 
+template <class Ar>
+int launch_polymat(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* A,
+                   const typename Ar::word* B, int n, long long d, typename Ar::word* C,
+                   typename Ar::word* ws, typename Ar::tw inv_scale, typename Ar::tw r, cudaStream_t st);
+
 // Launch shape of the fused product kernels for one (word size, log2 n):
 // lppc  log2 of products per block (one-block sizes),
 // logw  log2 of columns per block in the column passes,
@@ -60,6 +65,8 @@ size_t tile_smem_bytes(unsigned word_bytes, int logL, int lognvec);
 // Launch profiling hooks (no-ops unless ntt_profile_begin() is active).
 void prof_begin_call(cudaStream_t st);
 void prof_mark(cudaStream_t st, const char* name);
+
+int modmul_rate(uint64_t p, unsigned kind, unsigned word_bytes, int iters, double* per_s);
 
 int launch_modmul_vec(uint64_t p, unsigned kind, unsigned word_bytes, const uint64_t* x,
                       const uint64_t* y, const uint64_t* yc, uint64_t* z, size_t n, cudaStream_t st);

@@ -201,6 +201,106 @@ __global__ void k_modmul_vec(MMArgs A, const uint64_t* __restrict__ x, const uin
     }
 }
 
+// Throughput of one reduction: every thread runs 4 independent chains of
+// `iters` dependent modular products on register values (x <- x y rem p),
+// so the result measures the variant's arithmetic, not memory.
+template <int KIND, int WB>
+__global__ void k_modmul_rate(MMArgs A, uint64_t* out, int iters, uint64_t y, uint64_t yc) {
+    uint64_t v[4];
+    for (int c = 0; c < 4; ++c) v[c] = (threadIdx.x * 7919u + c * 104729u + blockIdx.x) % A.p;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint64_t x = v[c];
+            if (WB == 4) {
+                const uint32_t p = static_cast<uint32_t>(A.p);
+                const uint32_t x32 = static_cast<uint32_t>(x), y32 = static_cast<uint32_t>(y);
+                if (KIND == NTT_MM_BARRETT) x = barrett32(static_cast<uint64_t>(x32) * y32, p, A.bar);
+                if (KIND == NTT_MM_SHOUP) {
+                    const uint32_t q = __umulhi(x32, static_cast<uint32_t>(yc));
+                    const uint64_t d = static_cast<uint64_t>(x32) * y32 - static_cast<uint64_t>(q) * p;
+                    x = (d >= p) ? d - p : d;
+                }
+                if (KIND == NTT_MM_MONTGOMERY) {
+                    x = redc32(static_cast<uint64_t>(x32) * y32, p, static_cast<uint32_t>(A.chi));
+                }
+                if (KIND == NTT_MM_MONT_FIXED) {
+                    const Mont32 ar{p, static_cast<uint32_t>(A.pinv)};
+                    x = ar.mulw(x32, Tw32{y32, static_cast<uint32_t>(yc)});
+                }
+            } else {
+                if (KIND == NTT_MM_BARRETT) x = barrett64(static_cast<u128>(x) * y, A.p, A.bar);
+                if (KIND == NTT_MM_SHOUP) x = Shoup64L{A.p, A.pinv}.canon(Shoup64L{A.p, A.pinv}.mulw(x, Tw64{y, yc}));
+                if (KIND == NTT_MM_MONTGOMERY) x = redc64(static_cast<u128>(x) * y, A.p, A.chi);
+            }
+            if (KIND == NTT_MM_FMA)
+                x = fma_mulmod(static_cast<double>(x), static_cast<double>(y), A.dp, A.u);
+            v[c] = x;
+        }
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = v[0] ^ v[1] ^ v[2] ^ v[3];
+}
+
+int modmul_rate(uint64_t p, unsigned kind, unsigned word_bytes, int iters, double* per_s) {
+    if (kind > NTT_MM_MONT_FIXED || (word_bytes != 4 && word_bytes != 8) || iters <= 0 || !per_s)
+        return NTT_ERR_ARG;
+    if (p < 3 || !(p & 1) || (word_bytes == 4 && (p >> 32)) || (word_bytes == 8 && (p >> 62)) ||
+        (kind == NTT_MM_FMA && (p >> 50)) || (kind == NTT_MM_MONT_FIXED && word_bytes != 4))
+        return NTT_ERR_MODULUS;
+    MMArgs A{};
+    A.p = p;
+    A.kind = kind;
+    A.wb = word_bytes;
+    const unsigned nbits = word_bytes * 8;
+    A.bar = barrett_params(p, nbits);
+    if (nbits == 32) {
+        A.pinv = host::inv_pow2_32(static_cast<uint32_t>(p));
+        A.chi = static_cast<uint32_t>(0u - static_cast<uint32_t>(A.pinv));
+    } else {
+        A.pinv = host::inv_pow2_64(p);
+        A.chi = 0 - A.pinv;
+    }
+    A.dp = static_cast<double>(p);
+    A.u = 1.0 / A.dp;
+    const uint64_t y = p / 3 + 1;
+    uint64_t yc = 0;
+    if (kind == NTT_MM_SHOUP) yc = static_cast<uint64_t>((static_cast<u128>(y) << nbits) / p);
+    if (kind == NTT_MM_MONT_FIXED) yc = host::tw32_of(y, static_cast<uint32_t>(p), static_cast<uint32_t>(A.pinv)).c;
+    uint64_t ymf = y;
+    if (kind == NTT_MM_MONT_FIXED) ymf = host::tw32_of(y, static_cast<uint32_t>(p), static_cast<uint32_t>(A.pinv)).w;
+    const int blocks = 152 * 8, threads = 256;
+    uint64_t* out = nullptr;
+    if (cudaMalloc(&out, sizeof(uint64_t) * blocks * threads) != cudaSuccess) return NTT_ERR_OOM;
+    auto launch = [&](int it) {
+#define GBNTT_RATE(K, W) \
+    if (kind == K && word_bytes == W) k_modmul_rate<K, W><<<blocks, threads>>>(A, out, it, ymf, yc);
+        GBNTT_RATE(NTT_MM_BARRETT, 4) GBNTT_RATE(NTT_MM_SHOUP, 4) GBNTT_RATE(NTT_MM_MONTGOMERY, 4)
+        GBNTT_RATE(NTT_MM_FMA, 4) GBNTT_RATE(NTT_MM_MONT_FIXED, 4) GBNTT_RATE(NTT_MM_BARRETT, 8)
+        GBNTT_RATE(NTT_MM_SHOUP, 8) GBNTT_RATE(NTT_MM_MONTGOMERY, 8) GBNTT_RATE(NTT_MM_FMA, 8)
+#undef GBNTT_RATE
+    };
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    launch(16);
+    cudaEventRecord(e0);
+    launch(iters);
+    cudaEventRecord(e1);
+    int rc = NTT_OK;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = NTT_ERR_CUDA;
+    } else {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *per_s = 4.0 * iters * blocks * threads / (ms * 1e-3);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    cudaGetLastError();
+    return rc;
+}
+
 int launch_modmul_vec(uint64_t p, unsigned kind, unsigned word_bytes, const uint64_t* x,
                       const uint64_t* y, const uint64_t* yc, uint64_t* z, size_t n, cudaStream_t st) {
     if (kind > NTT_MM_SUB || (word_bytes != 4 && word_bytes != 8)) return NTT_ERR_ARG;

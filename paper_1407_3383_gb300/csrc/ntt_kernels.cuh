@@ -408,6 +408,57 @@ k_batch_small(const DevPlan<Ar>* __restrict__ plans, const BatchDesc* __restrict
     }
 }
 
+// ------------------------------------------------------------------ polynomial matrices
+
+// Zero-padded copy of the 2 n^2 entries (A then B, d coefficients each) into
+// rows of 2^logN words.
+template <class Ar>
+__global__ void k_polymat_pad(const typename Ar::word* __restrict__ A, const typename Ar::word* __restrict__ B,
+                              typename Ar::word* __restrict__ ws, long long nn, long long d, int logN) {
+    const long long N = 1LL << logN;
+    const long long total = (2 * nn) << logN;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long e = idx >> logN, k = idx & (N - 1);
+        typename Ar::word x = 0;
+        if (k < d) x = (e < nn) ? A[e * d + k] : B[(e - nn) * d + k];
+        ws[idx] = x;
+    }
+}
+
+// At every frequency k: C^(k) = A^(k) B^(k), an n x n matrix product over
+// F_p.  Sums of Montgomery products carry a factor 2^-w, removed at the end
+// by the fixed product with r = 2^w rem p.
+template <class Ar>
+__global__ void k_polymat_freq(Ar ar, const typename Ar::word* __restrict__ At,
+                               const typename Ar::word* __restrict__ Bt, typename Ar::word* __restrict__ Ct,
+                               int n, int logN, typename Ar::tw r) {
+    const long long N = 1LL << logN;
+    const long long total = static_cast<long long>(n) * n << logN;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long k = idx & (N - 1);
+        const long long e = idx >> logN;
+        const int i = static_cast<int>(e / n), j = static_cast<int>(e % n);
+        typename Ar::word acc = 0;
+        for (int l = 0; l < n; ++l)
+            acc = ar.add(acc, ar.mulmont(At[((long long)(i * n + l) << logN) + k],
+                                         Bt[((long long)(l * n + j) << logN) + k]));
+        Ct[idx] = ar.mulw(acc, r);
+    }
+}
+
+template <class Ar>
+__global__ void k_polymat_crop(Ar ar, const typename Ar::word* __restrict__ ws, typename Ar::word* __restrict__ C,
+                               long long nn, long long dc, int logN) {
+    const long long total = nn * dc;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long e = idx / dc, k = idx - e * dc;
+        C[idx] = ar.canon(ws[(e << logN) + k]);
+    }
+}
+
 // ------------------------------------------------------------------ plain kernels
 
 template <class Ar>
@@ -652,6 +703,37 @@ int launch_batch_bucket(const ntt_plan* plan, const DevPlan<Ar>& dp, const typen
         prof_mark(st, "k_col_inv");
     }
     return check_launch("batch bucket passes");
+}
+
+// forward declaration (defined below)
+template <class Ar>
+int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* data, long long batch,
+               bool fwd, typename Ar::tw scale, cudaStream_t st);
+
+// Polynomial matrix product (Section 5.2): transforms of every entry, n x n
+// products at every frequency, inverse transforms of the entries of C.
+// ws: 3 n^2 rows of n words.
+template <class Ar>
+int launch_polymat(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* A,
+                   const typename Ar::word* B, int n, long long d, typename Ar::word* C,
+                   typename Ar::word* ws, typename Ar::tw inv_scale, typename Ar::tw r, cudaStream_t st) {
+    const int k = static_cast<int>(plan->log2n);
+    const long long N = 1LL << k, nn = static_cast<long long>(n) * n;
+    typename Ar::word* At = ws;
+    typename Ar::word* Bt = ws + nn * N;
+    typename Ar::word* Ct = ws + 2 * nn * N;
+    prof_begin_call(st);
+    k_polymat_pad<Ar><<<grid_for(2 * nn * N), kThreads, 0, st>>>(A, B, ws, nn, d, k);
+    prof_mark(st, "k_polymat_pad");
+    int rc = launch_ntt<Ar>(plan, dp, At, 2 * nn, true, inv_scale, st);
+    if (rc != NTT_OK) return rc;
+    k_polymat_freq<Ar><<<grid_for(nn * N), kThreads, 0, st>>>(dp.ar, At, Bt, Ct, n, k, r);
+    prof_mark(st, "k_polymat_freq");
+    rc = launch_ntt<Ar>(plan, dp, Ct, nn, false, inv_scale, st);
+    if (rc != NTT_OK) return rc;
+    k_polymat_crop<Ar><<<grid_for(nn * (2 * d - 1)), kThreads, 0, st>>>(dp.ar, Ct, C, nn, 2 * d - 1, k);
+    prof_mark(st, "k_polymat_crop");
+    return check_launch("polymat kernels");
 }
 
 template <class Ar>

@@ -29,6 +29,8 @@ struct ntt_plan {
     // scaling constants, already in the policy's multiplicand form
     gbntt::Tw32 inv_scale32{}, pm_scale32{};   // n^-1 ; n^-1 * 2^32 (after Montgomery products)
     gbntt::Tw64 inv_scale64{}, pm_scale64{};   // n^-1 ; n^-1 * 2^64
+    gbntt::Tw32 r32{};                          // 2^32 rem p (undoes a Montgomery product)
+    gbntt::Tw64 r64{};                          // 2^64 rem p
 };
 
 // Three-prime integer product plan (intmul.cu): the primes, a transform plan

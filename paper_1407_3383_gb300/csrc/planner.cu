@@ -402,6 +402,7 @@ extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_p
         rc = finish_plan<Mont32, Tw32>(P, P->dp32, conv, (1ull << 32) % p);
         P->inv_scale32 = conv(P->n_inv);
         P->pm_scale32 = conv(mul_mod(P->n_inv, (1ull << 32) % p, p));
+        P->r32 = conv((1ull << 32) % p);
     } else {
         const uint64_t pinv = inv_pow2_64(p);
         P->dp64.ar = Shoup64L{p, pinv};
@@ -410,6 +411,7 @@ extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_p
         rc = finish_plan<Shoup64L, Tw64>(P, P->dp64, conv, r64);
         P->inv_scale64 = conv(P->n_inv);
         P->pm_scale64 = conv(mul_mod(P->n_inv, r64, p));
+        P->r64 = conv(r64);
     }
     if (rc != NTT_OK) {
         if (P->d_tables) cudaFree(P->d_tables);

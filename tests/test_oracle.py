@@ -405,3 +405,36 @@ def test_uniform_mod_deterministic_and_in_range():
     # with p = 3 every residue appears with frequency close to 1/3
     x = W.SplitMix64(8).uniform_mod(3, 30000)
     assert np.all(np.abs(np.bincount(x.astype(np.int64)) - 10000) < 400)
+
+
+# ---------------------------------------------------------------- polynomial matrices
+
+def test_polymat_mul_reduces_to_polymul_and_identity():
+    p = W.P_TABLE11
+    g = W.SplitMix64(31)
+    A = g.uniform_mod(p, 1 * 1 * 40).reshape(1, 1, 40)
+    B = g.uniform_mod(p, 1 * 1 * 40).reshape(1, 1, 40)
+    assert (O.polymat_mul(p, A, B)[0, 0] == O.polymul(p, A[0, 0], B[0, 0])).all()
+    n, d = 4, 9
+    I = np.zeros((n, n, d), dtype=np.uint64)
+    for i in range(n):
+        I[i, i, 0] = 1
+    B = g.uniform_mod(p, n * n * d).reshape(n, n, d)
+    C = O.polymat_mul(p, I, B)
+    assert (C[:, :, :d] == B).all() and (C[:, :, d:] == 0).all()
+
+
+def test_polymat_mul_entry_sums():
+    """Each entry is the sum over l of separate products (Python big-int sums)."""
+    p = W.P_B
+    g = W.SplitMix64(32)
+    n, d = 3, 17
+    A = g.uniform_mod(p, n * n * d).reshape(n, n, d)
+    B = g.uniform_mod(p, n * n * d).reshape(n, n, d)
+    C = O.polymat_mul(p, A, B)
+    for i in range(n):
+        for j in range(n):
+            acc = np.zeros(2 * d - 1, dtype=object)
+            for l in range(n):
+                acc = acc + O.polymul(p, A[i, l], B[l, j]).astype(object)
+            assert (C[i, j].astype(object) == acc % p).all()
