@@ -331,6 +331,22 @@ size_t intmul_workspace_size(const intmul_plan* plan, size_t na, size_t nb);
 int intmul_crt(const intmul_plan* plan, const uint32_t* d_a, size_t na, const uint32_t* d_b,
                size_t nb, uint32_t* d_c, void* d_ws, size_t ws_bytes, void* stream);
 
+/* Workspace bytes intmat_mul needs for n x n matrices of na- and nb-limb entries. */
+size_t intmat_workspace_size(const intmul_plan* plan, unsigned n, size_t na, size_t nb);
+
+/* C = A B for n x n matrices of non-negative integers (Section 5.3's
+ * integer matrix product by modular transforms): every entry of A has na
+ * 32-bit limbs, every entry of B nb limbs; entry (i, j) of C receives
+ * na + nb + 1 limbs (a sum of n products of na + nb limbs each needs one
+ * limb more).  Entries are cut into 64-bit chunks, the polynomial matrix
+ * product is taken modulo each of the three primes (polymat_mul's method),
+ * and every coefficient (a sum of n d products below 2^128, d = the larger
+ * chunk count) is rebuilt by Garner's CRT and carried.  A: entry (i, j) at
+ * limb (i n + j) na; B likewise with nb; C with na + nb + 1.  1 <= n <= 255.
+ * The plan must cover transforms of length >= 2d - 1. */
+int intmat_mul(const intmul_plan* plan, const uint32_t* d_A, size_t na, const uint32_t* d_B, size_t nb,
+               unsigned n, uint32_t* d_C, void* d_ws, size_t ws_bytes, void* stream);
+
 /* ---- element-wise modular operations (Sections 2.1-2.3, 3.3) ----------- */
 
 /* z[i] = x[i] * y[i] rem p with the reduction `kind` (NTT_MM_*; kinds

@@ -125,6 +125,8 @@ def _load():
             "intmul_plan_destroy": (_int, [_vp]),
             "intmul_workspace_size": (_sz, [_vp, _sz, _sz]),
             "intmul_crt": (_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp]),
+            "intmat_workspace_size": (_sz, [_vp, _uint, _sz, _sz]),
+            "intmat_mul": (_int, [_vp, _vp, _sz, _vp, _sz, _uint, _vp, _vp, _sz, _vp]),
             "ntt_status_str": (ctypes.c_char_p, [_int]),
             "ntt_last_error": (ctypes.c_char_p, []),
             "ntt_version": (ctypes.c_char_p, []),
@@ -496,6 +498,16 @@ def ntt_modmul_rate(p: int, kind: int, word_bytes: int, iters: int = 2048) -> fl
     out = ctypes.c_double()
     _check(_load().ntt_modmul_rate(p, kind, word_bytes, iters, ctypes.byref(out)), "ntt_modmul_rate")
     return out.value
+
+
+def intmat_workspace_size(plan: IntmulPlan, n: int, na: int, nb: int) -> int:
+    return int(_load().intmat_workspace_size(plan.handle, n, na, nb))
+
+
+def intmat_mul(plan: IntmulPlan, A, na: int, B, nb: int, n: int, C, ws, stream=None):
+    ws_bytes = ws.numel() * ws.element_size()
+    _check(_load().intmat_mul(plan.handle, _ptr(A), na, _ptr(B), nb, n, _ptr(C), _ptr(ws), ws_bytes,
+                              _stream(stream)), "intmat_mul")
 
 
 # ---------------------------------------------------------------- conveniences

@@ -73,6 +73,23 @@ __global__ void k_split(const uint32_t* __restrict__ a, long long na, const uint
     }
 }
 
+// Integer matrices: entry e of A (na limbs) and of B (nb limbs) -> d chunks
+// each, reduced modulo each prime.  red layout per prime: [A entries | B
+// entries], d words per entry.
+__global__ void k_split_mat(const uint32_t* __restrict__ a, long long na, const uint32_t* __restrict__ b,
+                            long long nb, long long nn, long long d, uint64_t* __restrict__ red,
+                            long long red_stride, CrtArgs C) {
+    const long long total = 2 * nn * d;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long e = idx / d, k = idx - e * d;
+        const uint64_t ch = (e < nn) ? chunk_of(a + e * na, na, k) : chunk_of(b + (e - nn) * nb, nb, k);
+        red[idx] = reduce_chunk(ch, C.P1);
+        red[red_stride + idx] = reduce_chunk(ch, C.P2);
+        red[2 * red_stride + idx] = reduce_chunk(ch, C.P3);
+    }
+}
+
 // Garner reconstruction of every product coefficient into three 64-bit words.
 __global__ void k_crt(const uint64_t* __restrict__ r, long long r_stride, long long nc,
                       uint64_t* __restrict__ W, CrtArgs C) {
@@ -127,8 +144,13 @@ __device__ __forceinline__ void store_word(uint32_t* c, long long nlimbs, long l
 // of the whole block (agg).
 __global__ void __launch_bounds__(kCarryThreads)
 k_carry_local(const uint64_t* __restrict__ W, long long nc, long long nwords, uint32_t* __restrict__ c,
-              long long nlimbs, uint8_t* __restrict__ st, uint8_t* __restrict__ agg) {
+              long long nlimbs, uint8_t* __restrict__ st, uint8_t* __restrict__ agg, long long nblocks) {
     __shared__ uint8_t warp_tot[kCarryThreads / 32];
+    // entry blockIdx.y of a batch of integers laid out back to back
+    W += blockIdx.y * 3 * nc;
+    c += blockIdx.y * nlimbs;
+    st += blockIdx.y * nwords;
+    agg += blockIdx.y * nblocks;
     const long long j0 = static_cast<long long>(blockIdx.x) * kCarryBlock + threadIdx.x * kCarryPerThread;
     uint8_t s[kCarryPerThread];
     uint8_t tot = kProp;
@@ -168,9 +190,10 @@ k_carry_local(const uint64_t* __restrict__ W, long long nc, long long nwords, ui
     }
 }
 
-// Pass 2 (one block): carry into each block, from the block states in order.
+// Pass 2 (one block per entry): carry into each block, from the block states in order.
 __global__ void k_carry_blocks(uint8_t* __restrict__ agg, long long nblocks) {
     __shared__ uint8_t part[1024];
+    agg += blockIdx.x * nblocks;
     const int t = threadIdx.x;
     const long long per = (nblocks + blockDim.x - 1) / blockDim.x;
     const long long b0 = t * per, b1 = std::min(nblocks, b0 + per);
@@ -190,7 +213,10 @@ __global__ void k_carry_blocks(uint8_t* __restrict__ agg, long long nblocks) {
 // Pass 3: add the incoming carry of every word.
 __global__ void __launch_bounds__(kCarryThreads)
 k_carry_apply(long long nwords, uint32_t* __restrict__ c, long long nlimbs,
-              const uint8_t* __restrict__ st, const uint8_t* __restrict__ blk_carry) {
+              const uint8_t* __restrict__ st, const uint8_t* __restrict__ blk_carry, long long nblocks) {
+    c += blockIdx.y * nlimbs;
+    st += blockIdx.y * nwords;
+    blk_carry += blockIdx.y * nblocks;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nwords;
          j += (long long)gridDim.x * blockDim.x) {
         const uint8_t s = st[j];
@@ -342,16 +368,120 @@ extern "C" int intmul_crt(const intmul_plan* plan, const uint32_t* d_a, size_t n
     k_crt<<<grid_of(L.nc, 256), 256, 0, st>>>(res, L.nc, L.nc, W, C);
     prof_mark(st, "k_crt");
     k_carry_local<<<static_cast<unsigned>(L.nblocks), kCarryThreads, 0, st>>>(
-        W, L.nc, L.nwords, d_c, static_cast<long long>(na + nb), sst, agg);
+        W, L.nc, L.nwords, d_c, static_cast<long long>(na + nb), sst, agg, L.nblocks);
     prof_mark(st, "k_carry_local");
     k_carry_blocks<<<1, 1024, 0, st>>>(agg, L.nblocks);
     prof_mark(st, "k_carry_blocks");
     k_carry_apply<<<grid_of(L.nwords, kCarryThreads), kCarryThreads, 0, st>>>(
-        L.nwords, d_c, static_cast<long long>(na + nb), sst, agg);
+        L.nwords, d_c, static_cast<long long>(na + nb), sst, agg, L.nblocks);
     prof_mark(st, "k_carry_apply");
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         gbntt_set_error(std::string("intmul_crt: ") + cudaGetErrorString(e));
+        return NTT_ERR_CUDA;
+    }
+    return NTT_OK;
+}
+
+// ---------------------------------------------------------------- integer matrices
+
+namespace {
+
+struct MatLayout {
+    int log2n;
+    long long nn, d, nc, nwords, nblocks;
+    size_t off_red, off_res, off_W, off_st, off_agg, off_poly, total;
+};
+
+MatLayout mat_layout_of(const intmul_plan* P, unsigned n, size_t na, size_t nb) {
+    MatLayout L{};
+    L.nn = static_cast<long long>(n) * n;
+    L.d = static_cast<long long>(std::max((na + 1) / 2, (nb + 1) / 2));
+    L.nc = 2 * L.d - 1;
+    // a sum of n < 2^32 products of 2d-chunk operands: 2d words plus one
+    // word for the sum's top, which also receives the third CRT word of the
+    // highest coefficient
+    L.nwords = 2 * L.d + 1;
+    L.nblocks = (L.nwords + kCarryBlock - 1) / kCarryBlock;
+    int k = 1;
+    while ((1LL << k) < L.nc) ++k;
+    L.log2n = k;
+    size_t off = 0;
+    L.off_red = off;
+    off = align256(off + 3 * static_cast<size_t>(2 * L.nn * L.d) * 8);
+    L.off_res = off;
+    off = align256(off + 3 * static_cast<size_t>(L.nn * L.nc) * 8);
+    L.off_W = off;
+    off = align256(off + 3 * static_cast<size_t>(L.nn * L.nc) * 8);
+    L.off_st = off;
+    off = align256(off + static_cast<size_t>(L.nn * L.nwords));
+    L.off_agg = off;
+    off = align256(off + static_cast<size_t>(L.nn * L.nblocks));
+    L.off_poly = off;
+    L.total = align256(off + 3 * static_cast<size_t>(L.nn) * (size_t(1) << k) * 8);
+    (void)P;
+    return L;
+}
+
+}  // namespace
+
+extern "C" size_t intmat_workspace_size(const intmul_plan* plan, unsigned n, size_t na, size_t nb) {
+    if (!plan || n == 0 || na == 0 || nb == 0) return 0;
+    return mat_layout_of(plan, n, na, nb).total;
+}
+
+extern "C" int intmat_mul(const intmul_plan* plan, const uint32_t* d_A, size_t na, const uint32_t* d_B,
+                          size_t nb, unsigned n, uint32_t* d_C, void* d_ws, size_t ws_bytes, void* stream) {
+    if (!plan || !d_A || !d_B || !d_C || n == 0 || n > 255 || na == 0 || nb == 0) return NTT_ERR_ARG;
+    const MatLayout L = mat_layout_of(plan, n, na, nb);
+    if (L.log2n > static_cast<int>(plan->max_log2n)) {
+        gbntt_set_error("intmat_mul: entries larger than the plan was created for");
+        return NTT_ERR_SIZE;
+    }
+    // every coefficient of C is a sum of n d products below 2^128
+    if (static_cast<double>(n) * static_cast<double>(L.d) >= 3.6e16) return NTT_ERR_SIZE;
+    if (!d_ws || ws_bytes < L.total || (reinterpret_cast<uintptr_t>(d_ws) & 255)) {
+        gbntt_set_error("intmat_mul: workspace of " + std::to_string(L.total) +
+                        " bytes (256-byte aligned) required");
+        return NTT_ERR_WORKSPACE;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char* ws = static_cast<unsigned char*>(d_ws);
+    uint64_t* red = reinterpret_cast<uint64_t*>(ws + L.off_red);
+    uint64_t* res = reinterpret_cast<uint64_t*>(ws + L.off_res);
+    uint64_t* W = reinterpret_cast<uint64_t*>(ws + L.off_W);
+    uint8_t* sst = ws + L.off_st;
+    uint8_t* agg = ws + L.off_agg;
+    uint64_t* poly = reinterpret_cast<uint64_t*>(ws + L.off_poly);
+    CrtArgs C{plan->P[0], plan->P[1], plan->P[2], plan->inv12, plan->inv13, plan->inv23};
+    const long long red_stride = 2 * L.nn * L.d;
+    const long long nlimbs = static_cast<long long>(na + nb + 1);
+    prof_begin_call(st);
+    k_split_mat<<<grid_of(red_stride, 256), 256, 0, st>>>(d_A, static_cast<long long>(na), d_B,
+                                                          static_cast<long long>(nb), L.nn, L.d, red,
+                                                          red_stride, C);
+    prof_mark(st, "k_split_mat");
+    for (int i = 0; i < 3; ++i) {
+        const ntt_plan* np = plan->plans[i][L.log2n];
+        const uint64_t* Ai = red + i * red_stride;
+        int rc = launch_polymat<Shoup64L>(np, np->dp64, Ai, Ai + L.nn * L.d, static_cast<int>(n), L.d,
+                                          res + i * L.nn * L.nc, poly, np->inv_scale64, np->r64, st);
+        if (rc != NTT_OK) return rc;
+    }
+    k_crt<<<grid_of(L.nn * L.nc, 256), 256, 0, st>>>(res, L.nn * L.nc, L.nn * L.nc, W, C);
+    prof_mark(st, "k_crt");
+    const unsigned ny = static_cast<unsigned>(L.nn);
+    k_carry_local<<<dim3(static_cast<unsigned>(L.nblocks), ny), kCarryThreads, 0, st>>>(
+        W, L.nc, L.nwords, d_C, nlimbs, sst, agg, L.nblocks);
+    prof_mark(st, "k_carry_local");
+    k_carry_blocks<<<ny, 1024, 0, st>>>(agg, L.nblocks);
+    prof_mark(st, "k_carry_blocks");
+    k_carry_apply<<<dim3(static_cast<unsigned>(std::min<long long>(L.nblocks * 4, 4096)), ny), kCarryThreads, 0, st>>>(
+        L.nwords, d_C, nlimbs, sst, agg, L.nblocks);
+    prof_mark(st, "k_carry_apply");
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        gbntt_set_error(std::string("intmat_mul: ") + cudaGetErrorString(e));
         return NTT_ERR_CUDA;
     }
     return NTT_OK;
