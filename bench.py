@@ -92,8 +92,10 @@ def fused_kernel_ops(log2n: int, na: int, nb: int, batch: int, tile_max_log: int
     col_fwd = 2 * (n1 * transform_ops(n2) + step2)
     row = 3 * n2 * transform_ops(n1) + N * o["mulg"]
     col_inv = step2 + n1 * transform_ops(n2) + nc * o["mulw"]
-    return {"k_col_fwd": col_fwd * batch, "k_row_polymul": row * batch,
-            "k_col_inv": col_inv * batch}
+    ops = {"k_col_fwd": col_fwd * batch, "k_row_polymul": row * batch, "k_col_inv": col_inv * batch}
+    # the direct 2^16-point kernels do the same work in the same three launches
+    ops.update({name + "_d": v for name, v in ops.items()})
+    return ops
 
 
 def alg_bytes(na, nb, batch, wb):
@@ -204,7 +206,7 @@ def make_inputs():
     return p, a, b
 
 
-KERNEL_SOURCES = ["engine.cuh", "modarith.cuh", "ntt_kernels.cuh", "ntt_u32.cu", "ntt_u64.cu"]
+KERNEL_SOURCES = ["engine.cuh", "modarith.cuh", "direct.cuh", "ntt_kernels.cuh", "ntt_u32.cu", "ntt_u64.cu"]
 
 
 def source_hash() -> str:
@@ -358,6 +360,8 @@ def run_native(args, world, rank, local):
     tuned_ms = None if args.no_autotune else G.ntt_autotune(plan, batch, stream=stream)
     shape = dict(zip(["log2_products_per_block", "log2_columns_per_block", "log2_rows_per_block"],
                      G.ntt_tune_get(plan.word_bytes, log2n)))
+    shape["kernels"] = ("direct 256 x 256" if log2n == 16 and shape["log2_columns_per_block"] == 0
+                        else "generic")
 
     def flush():
         flush_buf.fill_(1)

@@ -297,8 +297,12 @@ int ntt_server_destroy(ntt_server* server);
  * best time in ms to *best_ms when non-null.  Synchronous. */
 int ntt_autotune(const ntt_plan* plan, size_t batch, void* stream, float* best_ms);
 /* The shape currently used for (word_bytes, log2n): products per block,
- * columns per block and rows per block, each as log2. */
+ * columns per block and rows per block, each as log2.  For n = 2^16 above
+ * the one-block limit, logw = 0 (the default) selects the direct
+ * 256 x 256 kernels, whose block shape is fixed (lrpc is then ignored). */
 int ntt_tune_get(unsigned word_bytes, unsigned log2n, int* lppc, int* logw, int* lrpc);
+/* Forget every tuned or imported shape (back to the defaults). */
+int ntt_tune_reset(void);
 /* Text form of the shape table ("word_bytes log2n lppc logw lrpc" lines):
  * export into buf (cap bytes; *len receives the length; buf may be NULL to
  * query it) and import such text back. */

@@ -111,6 +111,7 @@ def _load():
                                     ctypes.POINTER(_int)]),
             "ntt_tune_export": (_int, [ctypes.c_char_p, _sz, ctypes.POINTER(_sz)]),
             "ntt_tune_import": (_int, [ctypes.c_char_p]),
+            "ntt_tune_reset": (_int, []),
             "ntt_server_create": (_int, [_vp, ctypes.POINTER(_vp)]),
             "ntt_server_submit": (_int, [_vp, _uint, _uint, _vp, _sz, _vp, _sz, _vp, _uint,
                                          ctypes.POINTER(_u64)]),
@@ -447,6 +448,11 @@ def ntt_tune_export() -> str:
 
 def ntt_tune_import(text: str):
     _check(_load().ntt_tune_import(text.encode()), "ntt_tune_import")
+
+
+def ntt_tune_reset():
+    """Forget every tuned or imported launch shape."""
+    _check(_load().ntt_tune_reset(), "ntt_tune_reset")
 
 
 # ---------------------------------------------------------------- integer products

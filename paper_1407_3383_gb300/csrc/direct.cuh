@@ -1,0 +1,298 @@
+// Direct kernels for products of n = 2^16 = 256 x 256 points.
+//
+// The same decomposition as the generic global schedule (Algorithm 1 at the
+// global level, n = n2 x n1 with n1 = n2 = 256, and every 256-word line once
+// more split 16 x 16), but the two radix-16 passes of a line are arranged so
+// that global memory is read by the first pass straight into registers and
+// written by the last pass straight from registers.  Every word crosses
+// shared memory once per kernel (one store, one load), and the row kernel
+// keeps both operands' inner 16-point transforms, their pointwise product
+// and the first inverse pass of the product in one thread's registers.
+//
+// Positions and twiddles agree word for word with the generic engine:
+//   outer pass (sub-transform size 256): a thread owns column j1 of the
+//       16 x 16 split of a line and holds rows t = 0..15, i.e. line
+//       positions 16 t + j1; DIF-16, then w_256^(j1 [t]_4) on register t;
+//   inner pass (size 16): a thread owns block `blk`, positions 16 blk + t;
+//       DIF-16 (bit-mirrored result in place), then in the column kernel
+//       the global twiddle w_n^(c [pos]_8) of Algorithm 1's step 2.
+// The inverse kernels run the same passes in reverse with w^-1 (DIT), the
+// twiddle of each pass applied before its butterflies.
+#pragma once
+#include <cstdint>
+#include <cstring>
+#include <type_traits>
+
+#include "engine.cuh"
+
+namespace gbntt {
+
+constexpr int kDLog = 8;                         // line length 2^8 in both directions
+constexpr int kDLine = 1 << kDLog;
+constexpr int kDCols = 32;                       // columns per column block (one per lane)
+constexpr int kDThreads = 256;
+constexpr int kDGroups = kDThreads / kDCols;     // warps of a column block
+constexpr int kDItems = 16 / kDGroups;           // 16-point columns or blocks per thread
+static_assert(kDItems * kDGroups == 16, "column blocks cover 16 x 16 lines");
+
+__host__ __device__ constexpr size_t direct_col_smem_words() { return size_t(kDCols) * kDLine; }
+
+// A twiddle from a table of (multiplicand, companion) pairs.  CTW with the
+// 32-bit Montgomery policy reads the multiplicand w~ alone and forms its
+// companion w~ p^-1 rem 2^32 with one multiply: half the table traffic, and
+// half the registers when the compiler keeps a thread's twiddles live.
+template <class Ar, bool CTW>
+__device__ __forceinline__ typename Ar::tw load_tw(const Ar& ar, const typename Ar::tw* p) {
+    if constexpr (CTW && std::is_same<Ar, Mont32>::value) {
+        const uint32_t w = p->w;
+        return Tw32{w, w * ar.pinv};
+    } else {
+        return *p;
+    }
+}
+
+// Number of leading rows (of 256 words) of column c that lie inside an
+// operand of `len` words: row r holds word r*256 + c.
+__device__ __forceinline__ int dcol_rows(long long len, long long c) {
+    const long long lim = len - c;
+    if (lim <= 0) return 0;
+    return static_cast<int>(std::min<long long>(kDLine, (lim + kDLine - 1) >> kDLog));
+}
+
+// Pass 1: forward column transforms of 32 columns of one operand (blockIdx.z
+// selects a or b), zero padding beyond the operand's length, the global
+// twiddle, and the store into the workspace.  ZHALF: rows >= 128 are all
+// padding (both operands have at most n/2 words).
+template <class Ar, bool ZHALF>
+__global__ void __launch_bounds__(kDThreads)
+k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long len0,
+            const typename Ar::word* __restrict__ src1, long long len1, typename Ar::word* __restrict__ dst,
+            long long dst_stride, long long dst_off1, long long prod_base,
+            const BatchDesc* __restrict__ desc) {
+    using word = typename Ar::word;
+    using tw = typename Ar::tw;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    word* sm = reinterpret_cast<word*>(smraw);
+    const int v = threadIdx.x & (kDCols - 1), g = threadIdx.x / kDCols;
+    const long long c0 = static_cast<long long>(blockIdx.x) * kDCols;
+    const long long prod = prod_base + blockIdx.y;
+    const word* src;
+    long long len;
+    if (desc) {
+        const BatchDesc d = desc[prod];
+        src = blockIdx.z ? src1 + d.boff : src0 + d.aoff;
+        len = blockIdx.z ? d.nb : d.na;
+    } else {
+        len = blockIdx.z ? len1 : len0;
+        src = (blockIdx.z ? src1 : src0) + prod * len;
+    }
+    const int rows = dcol_rows(len, c0 + v);
+    const word* in = src + c0 + v;
+    const tw* ltab = P.line_fwd[kDLog];
+#pragma unroll
+    for (int i = 0; i < kDItems; ++i) {
+        const int j1 = g + kDGroups * i;
+        word x[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int row = 16 * t + j1;
+            x[t] = word(0);
+            if ((!ZHALF || t < 8) && row < rows) x[t] = in[static_cast<long long>(row) * kDLine];
+        }
+        dif_regs<Ar, 16, ZHALF>(P.ar, x, P.rc);
+#pragma unroll
+        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], ltab[j1 * 16 + t]);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) sm[(16 * t + j1) * kDCols + v] = x[t];
+    }
+    __syncthreads();
+    word* out = dst + prod * dst_stride + (blockIdx.z ? dst_off1 : 0) + c0 + v;
+    const tw* gt = P.glob_fwd + c0 + v;
+#pragma unroll
+    for (int i = 0; i < kDItems; ++i) {
+        const int blk = g + kDGroups * i;
+        word x[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) x[t] = sm[(16 * blk + t) * kDCols + v];
+        dif_regs<Ar, 16>(P.ar, x, P.rc);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const long long pos = 16 * blk + t;
+            out[pos * kDLine] = P.ar.mulw(x[t], gt[pos * kDLine]);
+        }
+    }
+}
+
+// 16 consecutive words of shared memory (16-byte aligned) as 16-byte vectors.
+template <class W> struct Vec16;
+template <> struct Vec16<uint32_t> { using type = uint4; };
+template <> struct Vec16<uint64_t> { using type = ulonglong2; };
+
+template <class word>
+__device__ __forceinline__ void sm_load16(const word* p, word (&x)[16]) {
+    using V = typename Vec16<word>::type;
+    constexpr int per = 16 / sizeof(word);
+#pragma unroll
+    for (int q = 0; q < 16 / per; ++q) {
+        const V v = reinterpret_cast<const V*>(p)[q];
+        word tmp[per];
+        memcpy(tmp, &v, 16);
+#pragma unroll
+        for (int e = 0; e < per; ++e) x[q * per + e] = tmp[e];
+    }
+}
+
+template <class word>
+__device__ __forceinline__ void sm_store16(word* p, const word (&x)[16]) {
+    using V = typename Vec16<word>::type;
+    constexpr int per = 16 / sizeof(word);
+#pragma unroll
+    for (int q = 0; q < 16 / per; ++q) {
+        word tmp[per];
+#pragma unroll
+        for (int e = 0; e < per; ++e) tmp[e] = x[q * per + e];
+        V v;
+        memcpy(&v, tmp, 16);
+        reinterpret_cast<V*>(p)[q] = v;
+    }
+}
+
+// Row-kernel shared layout: four pad words after every 16 positions
+// (stride 20 per block of 16, 336 per line).  A thread's 16 consecutive
+// positions of the inner pass are then 16-byte aligned and move as four
+// 16-byte vectors without bank conflicts (the 8 lanes of a quarter warp hit
+// 8 disjoint groups of 4 banks), and the scalar accesses of the outer passes
+// are conflict-free because the two lines a warp touches differ by 16 banks.
+struct RowLayout {
+    static constexpr int kBlk = 20;
+    static constexpr int kLine = 16 * kBlk + 16;
+    __device__ __forceinline__ static int at(int line, int pos) { return line * kLine + (pos >> 4) * kBlk + (pos & 15); }
+};
+
+constexpr int kDRowsPerBlock = 4;      // rows of each operand per row block (64 threads)
+constexpr int kDRowMinBlocks32 = 20;   // 32-bit words: 20 blocks per SM (48 registers, no spills)
+
+__host__ __device__ constexpr size_t direct_row_smem_words() { return size_t(2 * kDRowsPerBlock) * RowLayout::kLine; }
+
+// Pass 2: RPB rows of both transformed operands -> forward row transforms,
+// pointwise product (Montgomery), inverse row transforms of the product,
+// written over operand a in the workspace.  One thread per (row, j1); small
+// blocks keep the barrier-separated phases of neighbouring blocks apart.
+template <class Ar, int RPB>
+__global__ void __launch_bounds__(RPB * 16, sizeof(typename Ar::word) == 4 ? kDRowMinBlocks32 : 1)
+k_row_polymul_d(DevPlan<Ar> P, typename Ar::word* __restrict__ ws, long long ws_stride, long long prod_base) {
+    using word = typename Ar::word;
+    using tw = typename Ar::tw;
+    using RL = RowLayout;
+    constexpr long long N = 1LL << (2 * kDLog);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    word* sm = reinterpret_cast<word*>(smraw);
+    const int r0 = blockIdx.x * RPB;
+    word* base = ws + (prod_base + blockIdx.y) * ws_stride;
+    const int j1 = threadIdx.x & 15, r = threadIdx.x >> 4;
+    // outer forward pass of row r of operand i (line RPB i + r)
+    const tw* lf = P.line_fwd[kDLog];
+#pragma unroll 1
+    for (int i = 0; i < 2; ++i) {
+        const word* in = base + i * N + static_cast<long long>(r0 + r) * kDLine + j1;
+        word x[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) x[t] = in[16 * t];
+        dif_regs<Ar, 16>(P.ar, x, P.rc);
+#pragma unroll
+        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, lf + j1 * 16 + t));
+#pragma unroll
+        for (int t = 0; t < 16; ++t) sm[RL::at(RPB * i + r, 16 * t + j1)] = x[t];
+    }
+    __syncthreads();
+    // inner passes of both operands, pointwise product, inner inverse pass
+    {
+        const int blk = j1;
+        word xa[16], xb[16];
+        word* pa = sm + RL::at(r, 16 * blk);
+        word* pb = sm + RL::at(RPB + r, 16 * blk);
+        sm_load16(pa, xa);
+        sm_load16(pb, xb);
+        dif_regs<Ar, 16>(P.ar, xa, P.rc);
+        dif_regs<Ar, 16>(P.ar, xb, P.rc);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) xa[t] = P.ar.mulmont(xa[t], xb[t]);
+        dit_regs<Ar, 16>(P.ar, xa, P.rci);
+        sm_store16(pa, xa);
+    }
+    __syncthreads();
+    // outer inverse pass of row r of the product
+    {
+        const tw* li = P.line_inv[kDLog];
+        word x[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) x[t] = sm[RL::at(r, 16 * t + j1)];
+#pragma unroll
+        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, li + j1 * 16 + t));
+        dit_regs<Ar, 16>(P.ar, x, P.rci);
+        word* o = base + static_cast<long long>(r0 + r) * kDLine + j1;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) o[16 * t] = x[t];
+    }
+}
+
+// Pass 3: inverse global twiddle (with n^-1 and the Montgomery factor folded
+// into itab), inverse column transforms, canonical cropped store of the first
+// out_len words of each product.
+template <class Ar>
+__global__ void __launch_bounds__(kDThreads)
+k_col_inv_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src, long long src_stride,
+            typename Ar::word* __restrict__ dst, long long out_len, const typename Ar::tw* __restrict__ itab,
+            long long prod_base, const BatchDesc* __restrict__ desc) {
+    using word = typename Ar::word;
+    using tw = typename Ar::tw;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    word* sm = reinterpret_cast<word*>(smraw);
+    const int v = threadIdx.x & (kDCols - 1), g = threadIdx.x / kDCols;
+    const long long c0 = static_cast<long long>(blockIdx.x) * kDCols;
+    const long long prod = prod_base + blockIdx.y;
+    const word* in = src + prod * src_stride + c0 + v;
+    const tw* gt = itab + c0 + v;
+#pragma unroll
+    for (int i = 0; i < kDItems; ++i) {
+        const int blk = g + kDGroups * i;
+        word x[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const long long pos = 16 * blk + t;
+            x[t] = P.ar.mulw(in[pos * kDLine], load_tw<Ar, true>(P.ar, gt + pos * kDLine));
+        }
+        dit_regs<Ar, 16>(P.ar, x, P.rci);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) sm[(16 * blk + t) * kDCols + v] = x[t];
+    }
+    __syncthreads();
+    word* outp;
+    if (desc) {
+        const BatchDesc d = desc[prod];
+        outp = dst + d.coff;
+        out_len = static_cast<long long>(d.na) + d.nb - 1;
+    } else {
+        outp = dst + prod * out_len;
+    }
+    const int rows = dcol_rows(out_len, c0 + v);
+    word* o = outp + c0 + v;
+    const tw* ltab = P.line_inv[kDLog];
+#pragma unroll
+    for (int i = 0; i < kDItems; ++i) {
+        const int j1 = g + kDGroups * i;
+        word x[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) x[t] = sm[(16 * t + j1) * kDCols + v];
+#pragma unroll
+        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, ltab + j1 * 16 + t));
+        dit_regs<Ar, 16>(P.ar, x, P.rci);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const int row = 16 * t + j1;
+            if (row < rows) o[static_cast<long long>(row) * kDLine] = P.ar.canon(x[t]);
+        }
+    }
+}
+
+}  // namespace gbntt

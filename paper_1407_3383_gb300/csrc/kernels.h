@@ -56,6 +56,7 @@ struct LaunchCfg {
     int lppc, logw, lrpc;
 };
 LaunchCfg default_launch_cfg(unsigned word_bytes, int log2n, int tile_max_log);
+LaunchCfg generic_global_cfg(unsigned word_bytes, int log2n);
 LaunchCfg launch_cfg(unsigned word_bytes, int log2n, int tile_max_log);   // tuned or default
 void set_launch_cfg(unsigned word_bytes, int log2n, LaunchCfg cfg);
 void clear_launch_cfg(unsigned word_bytes, int log2n);

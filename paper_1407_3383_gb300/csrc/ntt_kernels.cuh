@@ -24,6 +24,7 @@
 #include <string>
 
 #include "../../include/gbntt.h"
+#include "direct.cuh"
 #include "kernels.h"
 #include "plan.h"
 
@@ -563,6 +564,40 @@ static int check_launch(const char* what) {
 
 static constexpr long long kMaxGridY = 65535;
 
+// The three direct 256 x 256 kernels (n = 2^16 above the one-block limit):
+// uniform batches (desc == null: product t at a + t*na, b + t*nb,
+// c + t*(na+nb-1)) or uneven ones (desc: offsets and lengths per product,
+// a, b, c the flat buffers).  ws holds 2n words per product.
+template <class Ar>
+int launch_polymul_direct(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
+                          long long na, const typename Ar::word* b, long long nb, long long batch,
+                          typename Ar::word* c, typename Ar::word* ws, const BatchDesc* desc,
+                          cudaStream_t st) {
+    using word = typename Ar::word;
+    constexpr long long N = 1LL << (2 * kDLog);
+    const size_t smem_c = direct_col_smem_words() * sizeof(word);
+    const bool zhalf = !desc && 2 * std::max(na, nb) <= N;
+    auto kcf = zhalf ? k_col_fwd_d<Ar, true> : k_col_fwd_d<Ar, false>;
+    auto kci = k_col_inv_d<Ar>;
+    auto krp = k_row_polymul_d<Ar, kDRowsPerBlock>;
+    const size_t smem_r = direct_row_smem_words() * sizeof(word);
+    if (allow_smem(kcf, smem_c) != cudaSuccess || allow_smem(kci, smem_c) != cudaSuccess ||
+        allow_smem(krp, smem_r) != cudaSuccess)
+        return check_launch("smem attr");
+    const auto* itab = static_cast<const typename Ar::tw*>(plan->glob_inv_pm);
+    for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
+        const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
+        kcf<<<dim3(kDLine / kDCols, nbat, 2), kDThreads, smem_c, st>>>(dp, a, na, b, nb, ws, 2 * N, N, p0, desc);
+        prof_mark(st, "k_col_fwd_d");
+        krp<<<dim3(kDLine / kDRowsPerBlock, nbat, 1), kDRowsPerBlock * 16, smem_r, st>>>(dp, ws, 2 * N, p0);
+        prof_mark(st, "k_row_polymul_d");
+        kci<<<dim3(kDLine / kDCols, nbat, 1), kDThreads, smem_c, st>>>(dp, ws, 2 * N, c, na + nb - 1,
+                                                                       itab, p0, desc);
+        prof_mark(st, "k_col_inv_d");
+    }
+    return check_launch("direct polymul passes");
+}
+
 template <class Ar>
 int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
                          long long na, const typename Ar::word* b, long long nb, long long batch,
@@ -587,6 +622,7 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
         }
         return check_launch("k_tile_polymul");
     }
+    if (cfg.logw == 0) return launch_polymul_direct<Ar>(plan, dp, a, na, b, nb, batch, c, ws, nullptr, st);
     const int k2 = plan->k2, k1 = plan->k1;
     const long long N = 1LL << k;
     const int logw = cfg.logw;
@@ -679,6 +715,7 @@ int launch_batch_bucket(const ntt_plan* plan, const DevPlan<Ar>& dp, const typen
     using word = typename Ar::word;
     const int k = static_cast<int>(plan->log2n);
     const LaunchCfg cfg = launch_cfg(sizeof(word), k, plan->tile_max_log);
+    if (cfg.logw == 0) return launch_polymul_direct<Ar>(plan, dp, a, 0, b, 0, count, c, ws, d_desc, st);
     const int k2 = plan->k2, k1 = plan->k1;
     const long long N = 1LL << k;
     const int logw = cfg.logw, lrpc = cfg.lrpc;

@@ -45,6 +45,13 @@ LaunchCfg default_launch_cfg(unsigned word_bytes, int log2n, int tile_max_log) {
         c.lppc = (log2n <= kMaxLineLog) ? 4 : 0;
         return c;
     }
+    if (log2n == 2 * kDLog) return c;                  // logw = 0: the direct 256 x 256 kernels
+    return generic_global_cfg(word_bytes, log2n);
+}
+
+// Columns and rows per block of the generic global passes.
+LaunchCfg generic_global_cfg(unsigned word_bytes, int log2n) {
+    LaunchCfg c{0, 0, 0};
     const int k2 = log2n / 2, k1 = log2n - k2;
     int logw = (word_bytes == 4) ? 5 : 4;             // 128-byte row segments
     const int min_logw = (word_bytes == 4) ? 3 : 2;   // at least 32-byte sectors
@@ -60,6 +67,7 @@ static bool cfg_valid(unsigned wb, int k, int tile_max_log, const LaunchCfg& c) 
     const size_t cap = 227 * 1024;
     if (k <= tile_max_log) return c.lppc >= 0 && c.lppc <= 6 && tile_smem_bytes(wb, k, c.lppc + 1) <= cap;
     const int k2 = k / 2, k1 = k - k2;
+    if (c.logw == 0) return k == 2 * kDLog;
     return c.logw >= 1 && c.logw <= k1 && col_smem_bytes(wb, k2, c.logw) <= cap && c.lrpc >= 0 &&
            c.lrpc <= k2 && tile_smem_bytes(wb, k1, c.lrpc + 1) <= cap;
 }
@@ -153,22 +161,32 @@ extern "C" int ntt_autotune(const ntt_plan* plan, size_t batch, void* stream, fl
             if (t < best_t) best_t = t, best = cfg;
         }
     } else {
+        // generic shapes: columns per block, then rows per block, from the
+        // generic default; the direct kernels (logw = 0, n = 2^16 only)
+        // compete with the best of them
         const int k2 = k / 2, k1 = k - k2;
+        LaunchCfg g = best;
+        float g_t = best_t;
+        if (best.logw == 0) {
+            g = generic_global_cfg(wb, k);
+            g_t = try_cfg(g);
+        }
         for (int logw = 1; logw <= 6 && (1 << logw) <= (1 << k1); ++logw) {
             if (col_smem_bytes(wb, k2, logw) > kMaxSmem) break;
             if ((1 << logw) * wb < 16) continue;
-            LaunchCfg cfg = best;
+            LaunchCfg cfg = g;
             cfg.logw = logw;
             const float t = try_cfg(cfg);
-            if (t < best_t) best_t = t, best = cfg;
+            if (t < g_t) g_t = t, g = cfg;
         }
         for (int lrpc = 0; lrpc <= 6 && lrpc <= k2; ++lrpc) {
             if (tile_smem_bytes(wb, k1, lrpc + 1) > kMaxSmem) break;
-            LaunchCfg cfg = best;
+            LaunchCfg cfg = g;
             cfg.lrpc = lrpc;
             const float t = try_cfg(cfg);
-            if (t < best_t) best_t = t, best = cfg;
+            if (t < g_t) g_t = t, g = cfg;
         }
+        if (g_t < best_t) best_t = g_t, best = g;
     }
     set_launch_cfg(wb, k, best);
     if (best_ms) *best_ms = best_t;
@@ -190,6 +208,12 @@ extern "C" int ntt_tune_get(unsigned word_bytes, unsigned log2n, int* lppc, int*
     *lppc = c.lppc;
     *logw = c.logw;
     *lrpc = c.lrpc;
+    return NTT_OK;
+}
+
+extern "C" int ntt_tune_reset(void) {
+    std::lock_guard<std::mutex> lock(g_cfg_mu);
+    g_cfg.clear();
     return NTT_OK;
 }
 

@@ -47,6 +47,9 @@ def test_config0_single_product_full():
     (W.P_B, 14, 8192, 8192, 2),    # largest one-block tile (u32)
     (W.P_B, 15, 9000, 7001, 2),    # two global passes, ragged lengths
     (W.P_A, 16, 1 << 15, 1 << 15, 2),
+    (W.P_B, 16, 40000, 25535, 3),  # 2^16 points, operand a past n/2: no zero half
+    (W.P_B, 16, 33000, 1, 2),      # 2^16 points, degree-0 operand b
+    (W.P2, 16, 30001, 20000, 2),   # 2^16 points, 64-bit words
     (W.P1, 7, 64, 64, 21),
     (W.P2, 13, 4096, 4096, 2),     # largest one-block tile (u64)
     (W.P3, 14, 5000, 3000, 2),     # two global passes (u64)
@@ -147,3 +150,24 @@ def test_errors_are_reported():
         with pytest.raises(G.NttError) as e:
             G.polymul_mod_p_batch(plan, bad, 100, bad, 100, 1, c)
         assert e.value.status == 6
+
+
+@pytest.mark.parametrize("p", [W.P_B, W.P3])
+def test_direct_kernels_equal_generic_passes(p):
+    """At n = 2^16 the default shape (logw = 0) runs the direct 256 x 256
+    kernels; the generic column/row passes must give the same words."""
+    g = W.SplitMix64(616 + p % 1000)
+    a = g.uniform_mod(p, 3 * 30000).reshape(3, 30000)
+    b = g.uniform_mod(p, 3 * 27000).reshape(3, 27000)
+    wb = 4 if p < (1 << 32) else 8
+    G.ntt_tune_reset()
+    assert G.ntt_tune_get(wb, 16)[1] == 0
+    direct = _polymul(p, 16, a, b)
+    try:
+        G.ntt_tune_import(f"{wb} 16 0 {5 if wb == 4 else 4} 4\n")
+        generic = _polymul(p, 16, a, b)
+    finally:
+        G.ntt_tune_reset()
+    assert (direct == generic).all()
+    assert (direct[1] == O.polymul(p, a[1], b[1])).all()
+

@@ -11,6 +11,8 @@ def test_tune_table_round_trip():
     assert G.ntt_tune_get(4, 15) == (0, 4, 2)
     text = G.ntt_tune_export()
     assert "8 20 0 3 1" in text and "4 15 0 4 2" in text
+    G.ntt_tune_reset()
+    assert G.ntt_tune_export() == ""
 
 
 def test_tune_rejects_bad_shapes():
@@ -21,6 +23,12 @@ def test_tune_rejects_bad_shapes():
 
 
 def test_default_shapes():
+    G.ntt_tune_reset()
     # one-block sizes: 16 products per block for short vectors, 1 for tiles
     assert G.ntt_tune_get(4, 8)[0] == 4
     assert G.ntt_tune_get(8, 12)[0] == 0
+    # n = 2^16 above the one-block limit: the direct 256 x 256 kernels (logw = 0)
+    assert G.ntt_tune_get(4, 16)[1] == 0
+    assert G.ntt_tune_get(8, 16)[1] == 0
+    assert G.ntt_tune_get(4, 17)[1] >= 1
+
