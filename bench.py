@@ -53,9 +53,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None, choices=["fused"],
                     help="run only the fused timed steps (for profiler captures)")
-    ap.add_argument("--workload", default="polymul", choices=["polymul", "serve", "modmul"],
+    ap.add_argument("--workload", default="polymul", choices=["polymul", "serve", "modmul", "suite"],
                     help="polymul: the batched product (headline); serve: the Poisson "
-                         "stream of integer products through the serving loop")
+                         "stream of integer products through the serving loop; modmul: "
+                         "throughput of each reduction; suite: the other workloads and the "
+                         "matrix products, one context line each")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per stream")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape (profiler captures)")
@@ -589,6 +591,120 @@ def run_modmul(args, world, rank, local):
                           "unit": "Gmulmod/s", "results": res, "n_gpus": world}), flush=True)
 
 
+def run_suite(args, world, rank, local):
+    """Context lines for the workloads other than the headline: one 4096-point
+    product (latency, and graph-replayed rate), 1024 products of 2^12 words
+    and one 2^24-point transform mod P1, the 10,000-product uneven batch, the
+    polynomial matrix product at Table 15's largest shape and the integer
+    matrix product at Table 17's.  Device time with CUDA events on the
+    launching stream, L2 flushed before every timed repetition."""
+    import numpy as np
+    import torch
+    import paper_1407_3383_gb300 as G
+    from paper_1407_3383_gb300 import workloads as W
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def flush():
+        flush_buf.fill_(1)
+
+    def med(step, reps, warm=3):
+        for _ in range(warm):
+            step()
+        torch.cuda.synchronize()
+        return statistics.median(timed_steps(step, flush, reps, stream))
+
+    def emit(name, **kw):
+        if rank == 0:
+            print(json.dumps(dict(workload=name, n_gpus=world, context=True, **kw)), flush=True)
+
+    # one product of two length-2048 operands mod 998244353 (4096 points)
+    p, a, b = W.config0()
+    with G.Plan(p, 12) as plan:
+        da = torch.from_numpy(a.astype(np.uint32)).to(dev)
+        db = torch.from_numpy(b.astype(np.uint32)).to(dev)
+        dc = torch.empty(4095, dtype=torch.uint32, device=dev)
+        ms = med(lambda: G.polymul_mod_p(plan, da, 2048, db, 2048, dc, stream=stream), 50)
+        side = torch.cuda.Stream(device=dev)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            G.polymul_mod_p(plan, da, 2048, db, 2048, dc, stream=side)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(graph, stream=side):
+                for _ in range(100):
+                    G.polymul_mod_p(plan, da, 2048, db, 2048, dc, stream=side)
+        gms = med(lambda: graph.replay(), 10)
+        emit("1 product 2048 x 2048 mod 998244353 (4096 points, u32)",
+             us_per_product=1e3 * ms, graph_replayed_products_per_s=100 / (gms * 1e-3))
+
+    # 1024 products of length 2^12 mod P1 (2^13 points, u64)
+    p, a, b = W.config2_products()
+    with G.Plan(p, 13) as plan:
+        da = torch.from_numpy(a.reshape(-1)).to(dev)
+        db = torch.from_numpy(b.reshape(-1)).to(dev)
+        dc = torch.empty(1024 * 8191, dtype=torch.uint64, device=dev)
+        ms = med(lambda: G.polymul_mod_p_batch(plan, da, 4096, db, 4096, 1024, dc, stream=stream), 20)
+        emit("1024 products 2^12 x 2^12 mod P1 (2^13 points, u64)", ms=ms,
+             products_per_s=1024 / (ms * 1e-3), gbps_algorithmic=1024 * (2 * 4096 + 8191) * 8 / (ms * 1e-3) / 1e9)
+
+    # one 2^24-point transform mod P1, forward then inverse
+    p, x = W.config2_transform()
+    with G.Plan(p, 24) as plan:
+        dx = torch.from_numpy(x).to(dev)
+        fms = med(lambda: G.ntt_forward(plan, dx, 1, stream=stream), 10)
+        ims = med(lambda: G.ntt_inverse(plan, dx, 1, stream=stream), 10)
+        emit("one 2^24-point transform mod P1 (u64)", forward_ms=fms, inverse_ms=ims,
+             gbps_algorithmic_one_sweep_each=2 * 2 * (1 << 24) * 8 / ((fms + ims) * 1e-3) / 1e9)
+
+    # 10,000 uneven products, lengths log-uniform in [2^6, 2^18], primes P1..P3
+    lengths, pidx = W.config3_shapes()
+    _, al, bl = W.config3_operands(lengths, pidx)
+    with G.BatchPlan([W.P1, W.P2, W.P3], [v.size for v in al], [v.size for v in bl], pidx) as bp:
+        a = torch.from_numpy(np.concatenate(al)).to(dev)
+        b = torch.from_numpy(np.concatenate(bl)).to(dev)
+        c = torch.empty(bp.c_words, dtype=torch.uint64, device=dev)
+        ws = torch.empty(bp.workspace_size(), dtype=torch.uint8, device=dev)
+        modes = {}
+        for mode, nm in [(G.NTT_BATCH_DIRECT, "direct"), (G.NTT_BATCH_STREAMS, "streams"),
+                         (G.NTT_BATCH_GRAPH, "graph")]:
+            modes[nm + "_ms"] = med(lambda: bp.run(a, b, c, ws, mode, stream=stream), 5, warm=2)
+        del a, b, c, ws
+        emit("10,000 uneven products mod P1..P3 (u64)", **modes,
+             products_per_s=10000 / (min(modes.values()) * 1e-3))
+
+    # polynomial matrix product, n = 32, degree < 2^15 mod 469762049 (Table 15's largest)
+    p, n, d = W.P_TABLE11, 32, 1 << 15
+    g = W.SplitMix64(W.SEED_BASE + 15)
+    with G.Plan(p, 16) as plan:
+        A = torch.from_numpy(g.uniform_mod(p, n * n * d).astype(np.uint32)).to(dev)
+        B = torch.from_numpy(g.uniform_mod(p, n * n * d).astype(np.uint32)).to(dev)
+        C = torch.empty(n * n * (2 * d - 1), dtype=torch.uint32, device=dev)
+        ws = torch.empty(G.polymat_workspace_size(plan, n), dtype=torch.uint8, device=dev)
+        step = lambda: G.polymat_mul(plan, A, B, n, d, C, ws, stream=stream)
+        ms = med(step, 10)
+        per, _ = profile_window(G, step, flush, 3)
+        emit("polynomial matrix product 32 x 32, degree < 2^15, mod 469762049 (u32)", ms=ms,
+             kernels_ms={k: statistics.mean(v) for k, v in per.items()},
+             freq_mulmod_per_s=n ** 3 * (1 << 16) / (statistics.mean(per.get("k_polymat_freq", [ms])) * 1e-3))
+        del A, B, C, ws
+
+    # integer matrix product, n = 32, entries of 2^15 limbs (Table 17's shape)
+    n, na = 32, 1 << 15
+    g = W.SplitMix64(W.SEED_BASE + 17)
+    with G.IntmulPlan(1 << 16) as plan:
+        A = torch.from_numpy(g.limbs(n * n * na)).to(dev)
+        B = torch.from_numpy(g.limbs(n * n * na)).to(dev)
+        C = torch.empty(n * n * (2 * na + 1), dtype=torch.uint32, device=dev)
+        ws = torch.empty(G.intmat_workspace_size(plan, n, na, na), dtype=torch.uint8, device=dev)
+        step = lambda: G.intmat_mul(plan, A, na, B, na, n, C, ws, stream=stream)
+        ms = med(step, 5)
+        per, _ = profile_window(G, step, flush, 2)
+        emit("integer matrix product 32 x 32, entries of 2^15 limbs (2^20 bits)", ms=ms,
+             kernels_ms={k: statistics.mean(v) for k, v in per.items()})
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -596,6 +712,8 @@ def main():
         run_modmul(args, world, rank, local)
     elif args.workload == "serve" and args.impl == "native":
         run_serve(args, world, rank, local)
+    elif args.workload == "suite" and args.impl == "native":
+        run_suite(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)
     else:

@@ -171,8 +171,10 @@ struct RowLayout {
 
 constexpr int kDRowsPerBlock = 4;      // rows of each operand per row block (64 threads)
 constexpr int kDRowMinBlocks32 = 20;   // 32-bit words: 20 blocks per SM (48 registers, no spills)
+constexpr int kDNttRowsPerBlock = 8;   // standalone row transforms (128 threads)
 
 __host__ __device__ constexpr size_t direct_row_smem_words() { return size_t(2 * kDRowsPerBlock) * RowLayout::kLine; }
+__host__ __device__ constexpr size_t direct_ntt_row_smem_words() { return size_t(kDNttRowsPerBlock) * RowLayout::kLine; }
 
 // Pass 2: RPB rows of both transformed operands -> forward row transforms,
 // pointwise product (Montgomery), inverse row transforms of the product,
@@ -233,6 +235,53 @@ k_row_polymul_d(DevPlan<Ar> P, typename Ar::word* __restrict__ ws, long long ws_
         word* o = base + static_cast<long long>(r0 + r) * kDLine + j1;
 #pragma unroll
         for (int t = 0; t < 16; ++t) o[16 * t] = x[t];
+    }
+}
+
+// Standalone row transforms of 256 words (the second pass of a forward
+// 2^16-point transform, the first pass of an inverse one), in place, RPB rows
+// per block.  The inner pass faces global memory with 16-byte vectors (a
+// thread's 16 positions are consecutive), the outer pass with lanes over j1;
+// the two meet once in shared memory.  data must be 16-byte aligned.
+template <class Ar, bool FWD, int RPB>
+__global__ void __launch_bounds__(RPB * 16)
+k_row_ntt_d(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long prod_base) {
+    using word = typename Ar::word;
+    using tw = typename Ar::tw;
+    using RL = RowLayout;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    word* sm = reinterpret_cast<word*>(smraw);
+    const int j1 = threadIdx.x & 15, r = threadIdx.x >> 4;
+    word* line = data + ((prod_base + blockIdx.y) << (2 * kDLog)) + static_cast<long long>(blockIdx.x * RPB + r) * kDLine;
+    word x[16];
+    if (FWD) {
+        const tw* lf = P.line_fwd[kDLog];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) x[t] = line[16 * t + j1];
+        dif_regs<Ar, 16>(P.ar, x, P.rc);
+#pragma unroll
+        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, lf + j1 * 16 + t));
+#pragma unroll
+        for (int t = 0; t < 16; ++t) sm[RL::at(r, 16 * t + j1)] = x[t];
+        __syncthreads();
+        sm_load16(sm + RL::at(r, 16 * j1), x);
+        dif_regs<Ar, 16>(P.ar, x, P.rc);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) x[t] = P.ar.canon(x[t]);
+        sm_store16(line + 16 * j1, x);
+    } else {
+        const tw* li = P.line_inv[kDLog];
+        sm_load16(line + 16 * j1, x);
+        dit_regs<Ar, 16>(P.ar, x, P.rci);
+        sm_store16(sm + RL::at(r, 16 * j1), x);
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < 16; ++t) x[t] = sm[RL::at(r, 16 * t + j1)];
+#pragma unroll
+        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, li + j1 * 16 + t));
+        dit_regs<Ar, 16>(P.ar, x, P.rci);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) line[16 * t + j1] = x[t];
     }
 }
 

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <string>
 
 #include "../../include/gbntt.h"
@@ -430,22 +431,193 @@ __global__ void k_polymat_pad(const typename Ar::word* __restrict__ A, const typ
 // At every frequency k: C^(k) = A^(k) B^(k), an n x n matrix product over
 // F_p.  Sums of Montgomery products carry a factor 2^-w, removed at the end
 // by the fixed product with r = 2^w rem p.
-template <class Ar>
-__global__ void k_polymat_freq(Ar ar, const typename Ar::word* __restrict__ At,
-                               const typename Ar::word* __restrict__ Bt, typename Ar::word* __restrict__ Ct,
-                               int n, int logN, typename Ar::tw r) {
+// Step 2 of the polynomial matrix product: at every frequency k, the n x n
+// product C(k) = A(k) B(k).  One warp takes 32 consecutive frequencies (lanes
+// read consecutive words of every entry) and one 4 x 4 tile of C; the warps
+// of a block share the frequencies, so A's rows are reused from L1.
+// LAZY (32-bit words, K >= 3): the 64-bit products are summed in 64 bits and
+// folded into a residue every K terms (K (p-1)^2 < 2^64), so a term costs
+// one wide multiply-add; the fold is hi 2^32 + lo rem p by two fixed-
+// multiplicand products (r = 2^32 rem p, one = 1).  Otherwise every term is
+// a Montgomery product summed mod p and the sum is multiplied by r.
+template <class Ar, bool LAZY>
+__global__ void __launch_bounds__(256)
+k_polymat_freq(Ar ar, const typename Ar::word* __restrict__ At, const typename Ar::word* __restrict__ Bt,
+               typename Ar::word* __restrict__ Ct, int n, int logN, typename Ar::tw r, typename Ar::tw one,
+               int K) {
+    using word = typename Ar::word;
+    constexpr int T = 4;
     const long long N = 1LL << logN;
-    const long long total = static_cast<long long>(n) * n << logN;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long k = idx & (N - 1);
-        const long long e = idx >> logN;
-        const int i = static_cast<int>(e / n), j = static_cast<int>(e % n);
-        typename Ar::word acc = 0;
-        for (int l = 0; l < n; ++l)
-            acc = ar.add(acc, ar.mulmont(At[((long long)(i * n + l) << logN) + k],
-                                         Bt[((long long)(l * n + j) << logN) + k]));
-        Ct[idx] = ar.mulw(acc, r);
+    const int nt1 = (n + T - 1) / T;
+    const long long ntiles = static_cast<long long>(nt1) * nt1;
+    const long long warp = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const long long tile = warp % ntiles, kg = warp / ntiles;
+    const long long k = (kg << 5) + (threadIdx.x & 31);
+    if (k >= N) return;
+    const int i0 = static_cast<int>(tile / nt1) * T, j0 = static_cast<int>(tile % nt1) * T;
+    const word* a_base[T];
+    const word* b_base[T];
+#pragma unroll
+    for (int u = 0; u < T; ++u) {
+        a_base[u] = At + ((static_cast<long long>(min(i0 + u, n - 1)) * n) << logN) + k;   // row i0+u, l = 0
+        b_base[u] = Bt + (static_cast<long long>(min(j0 + u, n - 1)) << logN) + k;         // l = 0, column j0+u
+    }
+    const long long a_step = N, b_step = static_cast<long long>(n) << logN;
+    word res[T][T];
+#pragma unroll
+    for (int u = 0; u < T; ++u)
+#pragma unroll
+        for (int v = 0; v < T; ++v) res[u][v] = word(0);
+    if constexpr (LAZY) {
+        uint64_t acc[T][T];
+        for (int l0 = 0; l0 < n; l0 += K) {
+#pragma unroll
+            for (int u = 0; u < T; ++u)
+#pragma unroll
+                for (int v = 0; v < T; ++v) acc[u][v] = 0;
+            const int l1 = min(n, l0 + K);
+            for (int l = l0; l < l1; ++l) {
+                word a[T], b[T];
+#pragma unroll
+                for (int u = 0; u < T; ++u) {
+                    a[u] = a_base[u][l * a_step];
+                    b[u] = b_base[u][l * b_step];
+                }
+#pragma unroll
+                for (int u = 0; u < T; ++u)
+#pragma unroll
+                    for (int v = 0; v < T; ++v) acc[u][v] += static_cast<uint64_t>(a[u]) * b[v];
+            }
+#pragma unroll
+            for (int u = 0; u < T; ++u)
+#pragma unroll
+                for (int v = 0; v < T; ++v) {
+                    const word f = ar.add(ar.mulw(static_cast<word>(acc[u][v] >> 32), r),
+                                          ar.mulw(static_cast<word>(acc[u][v]), one));
+                    res[u][v] = ar.add(res[u][v], f);
+                }
+        }
+    } else {
+        for (int l = 0; l < n; ++l) {
+            word a[T], b[T];
+#pragma unroll
+            for (int u = 0; u < T; ++u) {
+                a[u] = a_base[u][l * a_step];
+                b[u] = b_base[u][l * b_step];
+            }
+#pragma unroll
+            for (int u = 0; u < T; ++u)
+#pragma unroll
+                for (int v = 0; v < T; ++v) res[u][v] = ar.add(res[u][v], ar.mulmont(a[u], b[v]));
+        }
+#pragma unroll
+        for (int u = 0; u < T; ++u)
+#pragma unroll
+            for (int v = 0; v < T; ++v) res[u][v] = ar.mulw(res[u][v], r);
+    }
+#pragma unroll
+    for (int u = 0; u < T; ++u)
+#pragma unroll
+        for (int v = 0; v < T; ++v)
+            if (i0 + u < n && j0 + v < n) Ct[((static_cast<long long>(i0 + u) * n + j0 + v) << logN) + k] = res[u][v];
+}
+
+// Shared-memory form of the per-frequency products for 32-bit words and
+// n in {8, 16, 32}: a block stages A(k) and B(k) for F consecutive
+// frequencies (entries read as F-word runs: whole 32-byte sectors), each
+// thread forms a 4 x 4 tile of one C(k) from shared memory (four scalar
+// words of A, one 16-byte vector of B per term) with 64-bit sums of the
+// products, and C goes back through shared memory as F-word runs.  A 64-bit
+// sum s = H 2^32 + L (any s < 2^64) is brought to s 2^-32 rem p by one
+// Montgomery reduction of t = H (2^32 rem p) + L < p 2^32; the final product
+// by r = 2^32 rem p removes the 2^-32.  Sums are folded every K terms.
+template <int NN>
+struct PmShared {
+    static constexpr int NT = NN / 4, TPF = NT * NT;            // tiles (threads) per frequency
+    static constexpr int F = (256 / TPF) > 8 ? (256 / TPF) : 8;  // frequencies per block
+    static constexpr int THREADS = F * TPF;
+    static constexpr int AS = NN + 1;                            // A row stride
+    static constexpr int AF = ((NN * AS + 31) / 32) * 32 + 4;    // A per frequency (4 banks apart)
+    static constexpr int BF = NN * NN + 4;                       // B (and C) per frequency
+    static constexpr size_t words = size_t(F) * (AF + BF);
+};
+
+template <int NN>
+__global__ void __launch_bounds__(PmShared<NN>::THREADS)
+k_polymat_freq_s(Mont32 ar, const uint32_t* __restrict__ At, const uint32_t* __restrict__ Bt,
+                 uint32_t* __restrict__ Ct, int logN, Tw32 r, uint32_t r1, int K) {
+    using S = PmShared<NN>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    uint32_t* sA = reinterpret_cast<uint32_t*>(smraw);
+    uint32_t* sB = sA + S::F * S::AF;
+    const long long N = 1LL << logN;
+    const long long k0 = static_cast<long long>(blockIdx.x) * S::F;
+    const int tid = threadIdx.x;
+#pragma unroll 4
+    for (int it = 0; it < NN * NN * S::F / S::THREADS; ++it) {
+        const int idx = it * S::THREADS + tid;
+        const int f = idx % S::F, e = idx / S::F;               // entry e = row * NN + column
+        const bool in = k0 + f < N;
+        const long long g = (static_cast<long long>(e) << logN) + k0 + f;
+        sA[f * S::AF + (e / NN) * S::AS + (e % NN)] = in ? At[g] : 0u;
+        sB[f * S::BF + e] = in ? Bt[g] : 0u;
+    }
+    __syncthreads();
+    const int f = tid / S::TPF, tile = tid % S::TPF;
+    const int i0 = (tile / S::NT) * 4, j0 = (tile % S::NT) * 4;
+    const uint32_t* a_f = sA + f * S::AF + i0 * S::AS;
+    const uint32_t* b_f = sB + f * S::BF + j0;
+    uint32_t res[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) res[u][v] = 0;
+    for (int l0 = 0; l0 < NN; l0 += K) {
+        uint64_t acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+        const int l1 = min(NN, l0 + K);
+        for (int l = l0; l < l1; ++l) {
+            uint32_t a[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = a_f[u * S::AS + l];
+            const uint4 bv = *reinterpret_cast<const uint4*>(b_f + l * NN);
+            const uint32_t b[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += static_cast<uint64_t>(a[u]) * b[v];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const uint64_t t = static_cast<uint64_t>(static_cast<uint32_t>(acc[u][v] >> 32)) * r1 +
+                                   static_cast<uint32_t>(acc[u][v]);
+                const uint32_t q = static_cast<uint32_t>(t) * ar.pinv;
+                const uint32_t red = ar.sub_sel(static_cast<uint32_t>(t >> 32), __umulhi(q, ar.p));
+                res[u][v] = ar.add(res[u][v], red);
+            }
+    }
+    __syncthreads();                                             // B is read; C reuses its space
+    uint32_t* c_f = sB + f * S::BF + i0 * NN + j0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        uint4 cv;
+        cv.x = ar.mulw(res[u][0], r);
+        cv.y = ar.mulw(res[u][1], r);
+        cv.z = ar.mulw(res[u][2], r);
+        cv.w = ar.mulw(res[u][3], r);
+        *reinterpret_cast<uint4*>(c_f + u * NN) = cv;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int it = 0; it < NN * NN * S::F / S::THREADS; ++it) {
+        const int idx = it * S::THREADS + tid;
+        const int ff = idx % S::F, e = idx / S::F;
+        if (k0 + ff < N) Ct[(static_cast<long long>(e) << logN) + k0 + ff] = sB[ff * S::BF + e];
     }
 }
 
@@ -598,6 +770,40 @@ int launch_polymul_direct(const ntt_plan* plan, const DevPlan<Ar>& dp, const typ
     return check_launch("direct polymul passes");
 }
 
+// Standalone 2^16-point transforms of `batch` vectors in place with the
+// direct kernels (data 16-byte aligned): forward = column pass with the
+// global twiddle, then row pass; inverse = row pass, then column pass with
+// the inverse global twiddle (n^-1 folded in).
+template <class Ar>
+int launch_ntt_direct(const DevPlan<Ar>& dp, typename Ar::word* data, long long batch, bool fwd,
+                      cudaStream_t st) {
+    using word = typename Ar::word;
+    constexpr long long N = 1LL << (2 * kDLog);
+    const size_t smem_c = direct_col_smem_words() * sizeof(word);
+    const size_t smem_r = direct_ntt_row_smem_words() * sizeof(word);
+    auto krow = fwd ? k_row_ntt_d<Ar, true, kDNttRowsPerBlock> : k_row_ntt_d<Ar, false, kDNttRowsPerBlock>;
+    if (allow_smem(k_col_fwd_d<Ar, false>, smem_c) != cudaSuccess ||
+        allow_smem(k_col_inv_d<Ar>, smem_c) != cudaSuccess || allow_smem(krow, smem_r) != cudaSuccess)
+        return check_launch("smem attr");
+    prof_begin_call(st);
+    for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
+        const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
+        const dim3 gc(kDLine / kDCols, nbat, 1), gr(kDLine / kDNttRowsPerBlock, nbat, 1);
+        if (fwd) {
+            k_col_fwd_d<Ar, false><<<gc, kDThreads, smem_c, st>>>(dp, data, N, data, N, data, N, 0, p0, nullptr);
+            prof_mark(st, "k_col_fwd_d");
+            krow<<<gr, kDNttRowsPerBlock * 16, smem_r, st>>>(dp, data, p0);
+            prof_mark(st, "k_row_ntt_fwd_d");
+        } else {
+            krow<<<gr, kDNttRowsPerBlock * 16, smem_r, st>>>(dp, data, p0);
+            prof_mark(st, "k_row_ntt_inv_d");
+            k_col_inv_d<Ar><<<gc, kDThreads, smem_c, st>>>(dp, data, N, data, N, dp.glob_inv, p0, nullptr);
+            prof_mark(st, "k_col_inv_d");
+        }
+    }
+    return check_launch("direct ntt passes");
+}
+
 template <class Ar>
 int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
                          long long na, const typename Ar::word* b, long long nb, long long batch,
@@ -747,6 +953,19 @@ template <class Ar>
 int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* data, long long batch,
                bool fwd, typename Ar::tw scale, cudaStream_t st);
 
+template <int NN>
+int launch_polymat_freq_s(const Mont32& ar, const uint32_t* At, const uint32_t* Bt, uint32_t* Ct, int logN,
+                          Tw32 r, int K, cudaStream_t st) {
+    using S = PmShared<NN>;
+    const size_t smem = S::words * sizeof(uint32_t);
+    if (allow_smem(k_polymat_freq_s<NN>, smem) != cudaSuccess) return check_launch("smem attr");
+    const long long N = 1LL << logN;
+    const uint32_t r1 = static_cast<uint32_t>((uint64_t(1) << 32) % ar.p);
+    k_polymat_freq_s<NN><<<static_cast<unsigned>((N + S::F - 1) / S::F), S::THREADS, smem, st>>>(
+        ar, At, Bt, Ct, logN, r, r1, K);
+    return NTT_OK;
+}
+
 // Polynomial matrix product (Section 5.2): transforms of every entry, n x n
 // products at every frequency, inverse transforms of the entries of C.
 // ws: 3 n^2 rows of n words.
@@ -759,13 +978,82 @@ int launch_polymat(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename A
     typename Ar::word* At = ws;
     typename Ar::word* Bt = ws + nn * N;
     typename Ar::word* Ct = ws + 2 * nn * N;
+    // n = 2^16 with the direct kernels: the column passes read the entries
+    // with their zero padding and write C cropped, so no pad or crop pass
+    const bool direct = k == 2 * kDLog && launch_cfg(sizeof(typename Ar::word), k, plan->tile_max_log).logw == 0;
     prof_begin_call(st);
-    k_polymat_pad<Ar><<<grid_for(2 * nn * N), kThreads, 0, st>>>(A, B, ws, nn, d, k);
-    prof_mark(st, "k_polymat_pad");
-    int rc = launch_ntt<Ar>(plan, dp, At, 2 * nn, true, inv_scale, st);
-    if (rc != NTT_OK) return rc;
-    k_polymat_freq<Ar><<<grid_for(nn * N), kThreads, 0, st>>>(dp.ar, At, Bt, Ct, n, k, r);
-    prof_mark(st, "k_polymat_freq");
+    int rc;
+    if (direct) {
+        constexpr long long NL = 1LL << (2 * kDLog);
+        const size_t smem_c = direct_col_smem_words() * sizeof(typename Ar::word);
+        const size_t smem_r = direct_ntt_row_smem_words() * sizeof(typename Ar::word);
+        const bool zh = 2 * d <= NL;
+        auto kcf = zh ? k_col_fwd_d<Ar, true> : k_col_fwd_d<Ar, false>;
+        if (allow_smem(kcf, smem_c) != cudaSuccess || allow_smem(k_col_inv_d<Ar>, smem_c) != cudaSuccess ||
+            allow_smem(k_row_ntt_d<Ar, true, kDNttRowsPerBlock>, smem_r) != cudaSuccess ||
+            allow_smem(k_row_ntt_d<Ar, false, kDNttRowsPerBlock>, smem_r) != cudaSuccess)
+            return check_launch("smem attr");
+        for (long long p0 = 0; p0 < nn; p0 += kMaxGridY) {
+            const unsigned nb = static_cast<unsigned>(std::min(nn - p0, kMaxGridY));
+            kcf<<<dim3(kDLine / kDCols, nb, 2), kDThreads, smem_c, st>>>(dp, A, d, B, d, ws, NL, nn * NL, p0,
+                                                                        nullptr);
+            prof_mark(st, "k_col_fwd_d");
+        }
+        for (long long p0 = 0; p0 < 2 * nn; p0 += kMaxGridY) {
+            const unsigned nb = static_cast<unsigned>(std::min(2 * nn - p0, kMaxGridY));
+            k_row_ntt_d<Ar, true, kDNttRowsPerBlock>
+                <<<dim3(kDLine / kDNttRowsPerBlock, nb, 1), kDNttRowsPerBlock * 16, smem_r, st>>>(dp, ws, p0);
+            prof_mark(st, "k_row_ntt_fwd_d");
+        }
+    } else {
+        k_polymat_pad<Ar><<<grid_for(2 * nn * N), kThreads, 0, st>>>(A, B, ws, nn, d, k);
+        prof_mark(st, "k_polymat_pad");
+        rc = launch_ntt<Ar>(plan, dp, At, 2 * nn, true, inv_scale, st);
+        if (rc != NTT_OK) return rc;
+    }
+    {
+        const long long nt1 = (n + 3) / 4, warps = nt1 * nt1 * ((N + 31) >> 5);
+        const unsigned blocks = static_cast<unsigned>((warps + 7) / 8);
+        typename Ar::tw one = r;
+        int K = 1;
+        if constexpr (std::is_same<Ar, Mont32>::value) {
+            const uint64_t p = dp.ar.p, pm1 = p - 1;
+            one.w = static_cast<uint32_t>((uint64_t(1) << 32) % p);     // 1 in Montgomery form
+            one.c = one.w * dp.ar.pinv;
+            K = pm1 == 0 ? 1 << 30 : static_cast<int>(std::min<uint64_t>(~uint64_t(0) / (pm1 * pm1), 1u << 30));
+        }
+        bool done = false;
+        if constexpr (std::is_same<Ar, Mont32>::value) {
+            if (n == 8 || n == 16 || n == 32) {
+                const int rc = n == 8    ? launch_polymat_freq_s<8>(dp.ar, At, Bt, Ct, k, r, K, st)
+                               : n == 16 ? launch_polymat_freq_s<16>(dp.ar, At, Bt, Ct, k, r, K, st)
+                                         : launch_polymat_freq_s<32>(dp.ar, At, Bt, Ct, k, r, K, st);
+                if (rc != NTT_OK) return rc;
+                done = true;
+            }
+        }
+        if (done) {
+        } else if (K >= 3)
+            k_polymat_freq<Ar, true><<<blocks, 256, 0, st>>>(dp.ar, At, Bt, Ct, n, k, r, one, K);
+        else
+            k_polymat_freq<Ar, false><<<blocks, 256, 0, st>>>(dp.ar, At, Bt, Ct, n, k, r, one, K);
+        prof_mark(st, "k_polymat_freq");
+    }
+    if (direct) {
+        constexpr long long NL = 1LL << (2 * kDLog);
+        const size_t smem_c = direct_col_smem_words() * sizeof(typename Ar::word);
+        const size_t smem_r = direct_ntt_row_smem_words() * sizeof(typename Ar::word);
+        for (long long p0 = 0; p0 < nn; p0 += kMaxGridY) {
+            const unsigned nb = static_cast<unsigned>(std::min(nn - p0, kMaxGridY));
+            k_row_ntt_d<Ar, false, kDNttRowsPerBlock>
+                <<<dim3(kDLine / kDNttRowsPerBlock, nb, 1), kDNttRowsPerBlock * 16, smem_r, st>>>(dp, Ct, p0);
+            prof_mark(st, "k_row_ntt_inv_d");
+            k_col_inv_d<Ar><<<dim3(kDLine / kDCols, nb, 1), kDThreads, smem_c, st>>>(dp, Ct, NL, C, 2 * d - 1,
+                                                                                    dp.glob_inv, p0, nullptr);
+            prof_mark(st, "k_col_inv_d");
+        }
+        return check_launch("polymat kernels");
+    }
     rc = launch_ntt<Ar>(plan, dp, Ct, nn, false, inv_scale, st);
     if (rc != NTT_OK) return rc;
     k_polymat_crop<Ar><<<grid_for(nn * (2 * d - 1)), kThreads, 0, st>>>(dp.ar, Ct, C, nn, 2 * d - 1, k);
@@ -791,7 +1079,11 @@ int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* d
     }
     const int k2 = plan->k2, k1 = plan->k1;
     const long long N = 1LL << k;
-    const int logw = launch_cfg(sizeof(word), k, plan->tile_max_log).logw;
+    int logw = launch_cfg(sizeof(word), k, plan->tile_max_log).logw;
+    if (logw == 0) {
+        if ((reinterpret_cast<uintptr_t>(data) & 15) == 0) return launch_ntt_direct<Ar>(dp, data, batch, fwd, st);
+        logw = generic_global_cfg(sizeof(word), k).logw;
+    }
     const size_t smem_c = slab_words(slab_layout(k2, logw)) * sizeof(word);
     const int lrpc = row_lrpc(k1, 1);
     const size_t smem_r = layout_words(tile_layout(k1, lrpc)) * sizeof(word);

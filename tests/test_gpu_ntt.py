@@ -63,6 +63,7 @@ def _check_sampled(p, log2n, a, fwd, batch, samples=48, seed=1):
     (W.P_A, 15, 2), (W.P_B, 16, 3), (W.P_A, 18, 1),      # two global passes (u32)
     (W.P1, 12, 2), (W.P3, 13, 2),                         # one block (u64)
     (W.P1, 14, 2), (W.P2, 17, 1), (W.P1, 20, 1),          # two global passes (u64)
+    (W.P3, 16, 3),                                        # direct 256 x 256 kernels (u64)
 ])
 def test_forward_sampled_and_roundtrip(p, log2n, batch):
     n = 1 << log2n
@@ -103,3 +104,31 @@ def test_convolution_theorem_on_device(p):
         fb, _ = _roundtrip(plan, pad(b), 1)
         fc, _ = _roundtrip(plan, c, 1)
     assert (fc == O.mulmod_vec(p, fa, fb)).all()
+
+
+@pytest.mark.parametrize("p", [W.P_B, W.P2])
+def test_2e16_direct_and_unaligned_generic_agree(p):
+    """2^16-point transforms of 16-byte-aligned data run the direct kernels;
+    data that is only word-aligned takes the generic passes.  Both must give
+    the oracle's values and the same words."""
+    import torch
+    log2n, batch = 16, 2
+    n = 1 << log2n
+    a = W.SplitMix64(p ^ 0x16).uniform_mod(p, batch * n)
+    with G.Plan(p, log2n) as plan:
+        G.ntt_tune_reset()
+        aligned = to_dev(a, plan.word_bytes)
+        G.ntt_forward(plan, aligned, batch)
+        buf = to_dev(np.zeros(batch * n + 1, dtype=np.uint64), plan.word_bytes)
+        shifted = buf[1:]                                  # one word off a 16-byte boundary
+        shifted.copy_(to_dev(a, plan.word_bytes))
+        G.ntt_forward(plan, shifted, batch)
+        torch.cuda.synchronize()
+        f1, f2 = from_dev(aligned), from_dev(shifted)
+        assert (f1 == f2).all()
+        _check_sampled(p, log2n, a, f1, batch)
+        G.ntt_inverse(plan, aligned, batch)
+        G.ntt_inverse(plan, shifted, batch)
+        torch.cuda.synchronize()
+        assert (from_dev(aligned) == a).all() and (from_dev(shifted) == a).all()
+

@@ -29,6 +29,10 @@ def _polymat(p, log2n, A, B):
 @pytest.mark.parametrize("p,n,d,log2n", [
     (W.P_TABLE11, 1, 1, 1), (W.P_TABLE11, 3, 5, 4), (W.P_B, 4, 100, 8), (W.P_A, 8, 700, 11),
     (W.P1, 3, 37, 7), (W.P2, 5, 3000, 13), (W.P3, 2, 9000, 15), (W.P_B, 2, 20000, 16),
+    (W.P_B, 16, 300, 10),          # shared-memory frequency kernel, one term per fold (p > 2^31)
+    (W.P_TABLE11, 32, 100, 8),     # shared-memory frequency kernel, one fold per output
+    (W.P_A, 32, 33, 7),            # 32 x 32 over 998244353 (several terms per fold)
+    (W.P_TABLE11, 8, 5, 4),        # fewer frequencies than a block holds
 ])
 def test_polymat_full(p, n, d, log2n):
     g = W.SplitMix64(p ^ (n * 1000 + d))
