@@ -53,11 +53,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None, choices=["fused"],
                     help="run only the fused timed steps (for profiler captures)")
-    ap.add_argument("--workload", default="polymul", choices=["polymul", "serve", "modmul", "suite"],
+    ap.add_argument("--workload", default="polymul", choices=["polymul", "serve", "modmul", "suite", "fp64"],
                     help="polymul: the batched product (headline); serve: the Poisson "
                          "stream of integer products through the serving loop; modmul: "
                          "throughput of each reduction; suite: the other workloads and the "
-                         "matrix products, one context line each")
+                         "matrix products, one context line each; fp64: transforms over "
+                         "doubles (Function 16) against the integer ones at Table 12's sizes")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per stream")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape (profiler captures)")
@@ -705,6 +706,42 @@ def run_suite(args, world, rank, local):
              kernels_ms={k: statistics.mean(v) for k, v in per.items()})
 
 
+def run_fp64(args, world, rank, local):
+    """Table 12's sizes (n = 2^8 .. 2^20, p = 1108307720798209): batched
+    forward transforms over doubles with Function 16 (NTT_FLAG_FP64) against
+    the integer Shoup transforms of the same prime, 2^24 words per launch,
+    device time per transform (CUDA events, L2 flushed before each)."""
+    import numpy as np
+    import torch
+    import paper_1407_3383_gb300 as G
+    from paper_1407_3383_gb300 import workloads as W
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    p = W.P_TABLE12
+    total = 1 << 24
+    x = W.SplitMix64(W.SEED_BASE + 12).uniform_mod(p, total)
+    rows = []
+    for log2n in range(8, 21):
+        batch = total >> log2n
+        res = {"log2n": log2n, "batch": batch}
+        for flag, name, dt in [(G.NTT_FLAG_FP64, "fp64_fma_us", np.float64), (0, "int_shoup_us", np.uint64)]:
+            with G.Plan(p, log2n, flag) as plan:
+                d = torch.from_numpy(x.astype(dt)).to(dev)
+                step = lambda: G.ntt_forward(plan, d, batch, stream=stream)
+                for _ in range(3):
+                    step()
+                torch.cuda.synchronize()
+                ms = statistics.median(timed_steps(step, lambda: flush_buf.fill_(1), 10, stream))
+                res[name] = 1e3 * ms / batch
+        res["int_over_fp64_speed"] = res["fp64_fma_us"] / res["int_shoup_us"]
+        rows.append(res)
+    if rank == 0:
+        print(json.dumps({"metric": "forward transform time per transform (us), Table 12 sizes",
+                          "p": p, "words_per_launch": total, "n_gpus": world, "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -714,6 +751,8 @@ def main():
         run_serve(args, world, rank, local)
     elif args.workload == "suite" and args.impl == "native":
         run_suite(args, world, rank, local)
+    elif args.workload == "fp64" and args.impl == "native":
+        run_fp64(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)
     else:

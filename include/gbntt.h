@@ -55,6 +55,8 @@ enum ntt_status {
 /* Plan creation flags. */
 #define NTT_FLAG_PLAIN 0x1u   /* also build the tables of the one-launch-per-stage schedule */
 #define NTT_FLAG_CHECK 0x2u   /* validate input ranges on the host side of each call */
+#define NTT_FLAG_FP64 0x4u    /* residues held as IEEE doubles, products by Function 16
+                                 (Section 3.3); needs p < 2^50; transforms and products only */
 
 /* Schedules for polymul_mod_p_batch. */
 #define NTT_SCHED_FUSED 0u    /* Algorithm 1 passes fused in shared memory */

@@ -26,6 +26,7 @@ HEADER = os.path.join(ROOT, "include", "gbntt.h")
 NTT_OK = 0
 NTT_FLAG_PLAIN = 0x1
 NTT_FLAG_CHECK = 0x2
+NTT_FLAG_FP64 = 0x4
 NTT_SCHED_FUSED = 0
 NTT_SCHED_PLAIN = 1
 NTT_MM_BARRETT = 0

@@ -20,6 +20,18 @@ static bool aligned(const void* ptr, size_t a) { return (reinterpret_cast<uintpt
 static int check_range(const ntt_plan* P, const void* d, size_t words, cudaStream_t st) {
     if (!(P->flags & NTT_FLAG_CHECK) || words == 0) return NTT_OK;
     std::vector<uint64_t> h(words);
+    if (P->flags & NTT_FLAG_FP64) {                      // doubles: integers in [0, p)
+        std::vector<double> hd(words);
+        if (cudaMemcpyAsync(hd.data(), d, words * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return NTT_ERR_CUDA;
+        for (size_t i = 0; i < words; ++i)
+            if (!(hd[i] >= 0.0 && hd[i] < static_cast<double>(P->p)) || hd[i] != static_cast<double>(static_cast<uint64_t>(hd[i]))) {
+                gbntt_set_error("input word " + std::to_string(i) + " is not an integer in [0, p)");
+                return NTT_ERR_RANGE;
+            }
+        return NTT_OK;
+    }
     if (P->word_bytes == 4) {
         std::vector<uint32_t> h32(words);
         if (cudaMemcpyAsync(h32.data(), d, words * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -49,6 +61,9 @@ static int ntt_dir(const ntt_plan* P, void* d_data, size_t batch, void* stream, 
         int rc = check_range(P, d_data, words, st);
         if (rc != NTT_OK) return rc;
     }
+    if (P->flags & NTT_FLAG_FP64)
+        return launch_ntt<Fma50>(P, P->dpf, static_cast<double*>(d_data), static_cast<long long>(batch), fwd,
+                                 P->inv_scalef, st);
     if (P->word_bytes == 4)
         return launch_ntt<Mont32>(P, P->dp32, static_cast<uint32_t*>(d_data),
                                   static_cast<long long>(batch), fwd, P->inv_scale32, st);
@@ -101,6 +116,10 @@ extern "C" int polymul_mod_p_batch(const ntt_plan* plan, const void* d_a, size_t
     if (rc != NTT_OK) return rc;
     const long long lna = static_cast<long long>(na), lnb = static_cast<long long>(nb);
     const long long lb = static_cast<long long>(batch);
+    if (P->flags & NTT_FLAG_FP64)                        // fused only (planning refuses PLAIN)
+        return launch_polymul_fused<Fma50>(P, P->dpf, static_cast<const double*>(d_a), lna,
+                                           static_cast<const double*>(d_b), lnb, lb, static_cast<double*>(d_c),
+                                           static_cast<double*>(d_ws), P->inv_scalef, st);
     if (wb == 4) {
         auto a = static_cast<const uint32_t*>(d_a);
         auto b = static_cast<const uint32_t*>(d_b);
@@ -142,6 +161,10 @@ extern "C" size_t polymat_workspace_size(const ntt_plan* plan, unsigned n) {
 extern "C" int polymat_mul(const ntt_plan* plan, const void* d_A, const void* d_B, unsigned n, size_t d,
                            void* d_C, void* d_ws, size_t ws_bytes, void* stream) {
     if (!plan || !d_A || !d_B || !d_C || n == 0 || n > 1024 || d == 0) return NTT_ERR_ARG;
+    if (plan->flags & NTT_FLAG_FP64) {
+        gbntt_set_error("polymat_mul: no FP64 form");
+        return NTT_ERR_UNSUPPORTED;
+    }
     if (2 * d - 1 > (size_t(1) << plan->log2n)) {
         gbntt_set_error("polymat_mul: 2d - 1 exceeds the plan's n");
         return NTT_ERR_SIZE;

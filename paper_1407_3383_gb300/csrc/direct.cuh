@@ -127,6 +127,7 @@ k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long
 template <class W> struct Vec16;
 template <> struct Vec16<uint32_t> { using type = uint4; };
 template <> struct Vec16<uint64_t> { using type = ulonglong2; };
+template <> struct Vec16<double> { using type = double2; };
 
 template <class word>
 __device__ __forceinline__ void sm_load16(const word* p, word (&x)[16]) {

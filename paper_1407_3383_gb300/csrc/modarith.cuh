@@ -151,4 +151,45 @@ struct Shoup64L {
     __device__ __forceinline__ uint64_t canon(uint64_t x) const { return (x >= p) ? x - p : x; }
 };
 
+// Fma50 -- residues as IEEE doubles, p < 2^50 (m <= l - 2 with l = 53 for
+// double).  Every product, twiddle or pointwise, is Function 16: the exact
+// product split by one FMA into h + l, the quotient c = floor(h u) with
+// u = 1/p rounded to nearest, d = h - c p by a second FMA, and e = d + l
+// corrected once by +-p (Proposition 13: correct for any rounding mode when
+// the product is below 2^(l-2) p).  Sums and differences stay in [0, p) with
+// one correction each (exact: sums are below 2^51).  There is no Montgomery
+// factor, so the pointwise product needs no extra scaling.
+struct TwF { double w; };
+
+struct Fma50 {
+    using word = double;
+    using tw = TwF;
+    static constexpr int kBits = 53;
+    double p;   // modulus < 2^50 (exact as a double)
+    double u;   // 1/p rounded to nearest
+
+    __device__ __forceinline__ double mul(double a, double b) const {
+        const double h = a * b;
+        const double l = fma(a, b, -h);
+        const double c = floor(h * u);
+        const double d = fma(-c, p, h);
+        const double e = d + l;
+        if (e >= p) return e - p;
+        return (e < 0.0) ? e + p : e;
+    }
+    __device__ __forceinline__ double add(double x, double y) const {
+        const double s = x + y;
+        return (s >= p) ? s - p : s;
+    }
+    __device__ __forceinline__ double sub(double x, double y) const {
+        const double d = x - y;
+        return (d < 0.0) ? d + p : d;
+    }
+    // Function 16 wants a non-negative product, so differences stay reduced
+    __device__ __forceinline__ double sub_lazy(double x, double y) const { return sub(x, y); }
+    __device__ __forceinline__ double canon(double x) const { return x; }
+    __device__ __forceinline__ double mulw(double x, TwF t) const { return mul(x, t.w); }
+    __device__ __forceinline__ double mulmont(double x, double y) const { return mul(x, y); }
+};
+
 }  // namespace gbntt

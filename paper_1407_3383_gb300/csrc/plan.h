@@ -10,7 +10,7 @@ struct ntt_plan {
     uint64_t p = 0;
     unsigned log2n = 0;
     unsigned flags = 0;
-    unsigned word_bytes = 0;    // 4 (p < 2^32) or 8 (p < 2^62)
+    unsigned word_bytes = 0;    // 4 (p < 2^32) or 8 (p < 2^62, or doubles with NTT_FLAG_FP64)
     unsigned v2 = 0;            // 2-adic valuation of p - 1
     uint64_t g = 0;             // least generator of F_p^*
     uint64_t omega = 0;         // g^((p-1)/n)
@@ -26,11 +26,13 @@ struct ntt_plan {
     size_t table_bytes = 0;
     gbntt::DevPlan<gbntt::Mont32> dp32{};
     gbntt::DevPlan<gbntt::Shoup64L> dp64{};
+    gbntt::DevPlan<gbntt::Fma50> dpf{};         // NTT_FLAG_FP64 plans
     // scaling constants, already in the policy's multiplicand form
     gbntt::Tw32 inv_scale32{}, pm_scale32{};   // n^-1 ; n^-1 * 2^32 (after Montgomery products)
     gbntt::Tw64 inv_scale64{}, pm_scale64{};   // n^-1 ; n^-1 * 2^64
     gbntt::Tw32 r32{};                          // 2^32 rem p (undoes a Montgomery product)
     gbntt::Tw64 r64{};                          // 2^64 rem p
+    gbntt::TwF inv_scalef{};                    // n^-1 (FP64 plans; no Montgomery factor)
 };
 
 // Three-prime integer product plan (intmul.cu): the primes, a transform plan

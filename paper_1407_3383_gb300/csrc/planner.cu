@@ -368,18 +368,26 @@ static int finish_plan(ntt_plan* P, DevPlan<Ar>& dp, Conv conv, uint64_t pm_fact
 extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_plan** out) {
     if (!out) return NTT_ERR_ARG;
     *out = nullptr;
-    if (log2n < 1 || log2n > 24 || (flags & ~(NTT_FLAG_PLAIN | NTT_FLAG_CHECK))) {
+    if (log2n < 1 || log2n > 24 || (flags & ~(NTT_FLAG_PLAIN | NTT_FLAG_CHECK | NTT_FLAG_FP64))) {
         gbntt_set_error("need 1 <= log2n <= 24 and known flags");
         return log2n > 24 ? NTT_ERR_SIZE : NTT_ERR_ARG;
     }
     int rc = check_modulus(p, log2n);
     if (rc != NTT_OK) return rc;
+    if ((flags & NTT_FLAG_FP64) && (p >> 50)) {
+        gbntt_set_error("NTT_FLAG_FP64 needs p < 2^50 (Function 16, m <= 50)");
+        return NTT_ERR_MODULUS;
+    }
+    if ((flags & NTT_FLAG_FP64) && (flags & NTT_FLAG_PLAIN)) {
+        gbntt_set_error("the one-launch-per-stage schedule has no FP64 form");
+        return NTT_ERR_UNSUPPORTED;
+    }
     ntt_plan* P = new (std::nothrow) ntt_plan();
     if (!P) return NTT_ERR_OOM;
     P->p = p;
     P->log2n = log2n;
     P->flags = flags;
-    P->word_bytes = (p >> 32) ? 8 : 4;
+    P->word_bytes = ((p >> 32) || (flags & NTT_FLAG_FP64)) ? 8 : 4;
     P->v2 = two_adic(p - 1);
     P->g = least_generator(p);
     P->omega = pow_mod(P->g, (p - 1) >> log2n, p);
@@ -394,7 +402,12 @@ extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_p
         delete P;
         return NTT_ERR_CUDA;
     }
-    if (P->word_bytes == 4) {
+    if (flags & NTT_FLAG_FP64) {
+        P->dpf.ar = Fma50{static_cast<double>(p), 1.0 / static_cast<double>(p)};
+        auto conv = [](uint64_t v) { return TwF{static_cast<double>(v)}; };
+        rc = finish_plan<Fma50, TwF>(P, P->dpf, conv, 1);
+        P->inv_scalef = conv(P->n_inv);
+    } else if (P->word_bytes == 4) {
         const uint32_t p32 = static_cast<uint32_t>(p);
         const uint32_t pinv = inv_pow2_32(p32);
         P->dp32.ar = Mont32{p32, pinv};

@@ -129,6 +129,10 @@ float time_product(const ntt_plan* P, const void* a, const void* b, void* c, voi
 
 extern "C" int ntt_autotune(const ntt_plan* plan, size_t batch, void* stream, float* best_ms) {
     if (!plan || batch == 0) return NTT_ERR_ARG;
+    if (plan->flags & NTT_FLAG_FP64) {        // the shape table is keyed by word size; FP64 plans share it
+        gbntt_set_error("ntt_autotune: tune the integer plan of the same word size instead");
+        return NTT_ERR_UNSUPPORTED;
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const unsigned wb = plan->word_bytes;
     const int k = static_cast<int>(plan->log2n);
