@@ -53,12 +53,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None, choices=["fused"],
                     help="run only the fused timed steps (for profiler captures)")
-    ap.add_argument("--workload", default="polymul", choices=["polymul", "serve", "modmul", "suite", "fp64"],
+    ap.add_argument("--workload", default="polymul", choices=["polymul", "serve", "modmul", "suite", "fp64", "tft"],
                     help="polymul: the batched product (headline); serve: the Poisson "
                          "stream of integer products through the serving loop; modmul: "
                          "throughput of each reduction; suite: the other workloads and the "
                          "matrix products, one context line each; fp64: transforms over "
-                         "doubles (Function 16) against the integer ones at Table 12's sizes")
+                         "doubles (Function 16) against the integer ones at Table 12's sizes; "
+                         "tft: 2^16-point products by output length class (truncated "
+                         "transforms against the full length)")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per stream")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape (profiler captures)")
@@ -742,6 +744,43 @@ def run_fp64(args, world, rank, local):
                           "p": p, "words_per_launch": total, "n_gpus": world, "rows": rows}), flush=True)
 
 
+def run_tft(args, world, rank, local):
+    """256 products mod 3*2^30+1 with n = 2^16 whose outputs need B of the 16
+    row blocks (na = nb = 2048 B): the truncated transforms (TFT, Section
+    5.1) against the full-length step that zero padding to n would cost."""
+    import numpy as np
+    import torch
+    import paper_1407_3383_gb300 as G
+    from paper_1407_3383_gb300 import workloads as W
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    p, batch = W.P_B, 256
+    g = W.SplitMix64(W.SEED_BASE + 51)
+    rows = []
+    with G.Plan(p, 16) as plan:
+        ws = G.alloc_workspace(plan, batch)
+        for beta in [16, 14, 12, 10, 8, 6, 4, 2, 1]:
+            na = nb = 2048 * beta
+            a = torch.from_numpy(g.uniform_mod(p, batch * na).astype(np.uint32)).to(dev)
+            b = torch.from_numpy(g.uniform_mod(p, batch * nb).astype(np.uint32)).to(dev)
+            c = torch.empty(batch * (na + nb - 1), dtype=torch.uint32, device=dev)
+            step = lambda: G.polymul_mod_p_batch(plan, a, na, b, nb, batch, c, G.NTT_SCHED_FUSED, ws,
+                                                 stream=stream)
+            for _ in range(3):
+                step()
+            torch.cuda.synchronize()
+            ms = statistics.median(timed_steps(step, lambda: flush_buf.fill_(1), 20, stream))
+            rows.append({"blocks": beta, "na": na, "nb": nb, "ms": ms, "products_per_s": batch / (ms * 1e-3)})
+    full = rows[0]["ms"]
+    for r in rows:
+        r["time_vs_padded"] = r["ms"] / full
+    if rank == 0:
+        print(json.dumps({"metric": "2^16-point products by output length (truncated transforms)",
+                          "p": p, "batch": batch, "n_gpus": world, "rows": rows}), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
@@ -753,6 +792,8 @@ def main():
         run_suite(args, world, rank, local)
     elif args.workload == "fp64" and args.impl == "native":
         run_fp64(args, world, rank, local)
+    elif args.workload == "tft" and args.impl == "native":
+        run_tft(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)
     else:

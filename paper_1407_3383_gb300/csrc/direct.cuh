@@ -24,6 +24,7 @@
 #include <type_traits>
 
 #include "engine.cuh"
+#include "tft.cuh"
 
 namespace gbntt {
 
@@ -51,6 +52,13 @@ __device__ __forceinline__ typename Ar::tw load_tw(const Ar& ar, const typename 
     }
 }
 
+// 16-row blocks of the column transforms that a product of `len` output
+// words needs (the TFT length rounded up to whole blocks: 1..16).
+__host__ __device__ inline int tft_blocks(long long len) {
+    const long long b = (len + 16 * kDLine - 1) / (16 * kDLine);
+    return static_cast<int>(b < 1 ? 1 : (b > 16 ? 16 : b));
+}
+
 // Number of leading rows (of 256 words) of column c that lie inside an
 // operand of `len` words: row r holds word r*256 + c.
 __device__ __forceinline__ int dcol_rows(long long len, long long c) {
@@ -62,13 +70,16 @@ __device__ __forceinline__ int dcol_rows(long long len, long long c) {
 // Pass 1: forward column transforms of 32 columns of one operand (blockIdx.z
 // selects a or b), zero padding beyond the operand's length, the global
 // twiddle, and the store into the workspace.  ZHALF: rows >= 128 are all
-// padding (both operands have at most n/2 words).
-template <class Ar, bool ZHALF>
+// padding (both operands have at most n/2 words).  TFT: only the first
+// 16 B rows of the transform are formed (B = beta, or from the descriptor's
+// product length): the truncated Fourier transform of Section 5.1 with
+// Algorithm 1's rows, its outer 16-point pass truncated to B outputs.
+template <class Ar, bool ZHALF, bool TFT = false>
 __global__ void __launch_bounds__(kDThreads)
 k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long len0,
             const typename Ar::word* __restrict__ src1, long long len1, typename Ar::word* __restrict__ dst,
             long long dst_stride, long long dst_off1, long long prod_base,
-            const BatchDesc* __restrict__ desc) {
+            const BatchDesc* __restrict__ desc, int beta) {
     using word = typename Ar::word;
     using tw = typename Ar::tw;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -78,13 +89,16 @@ k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long
     const long long prod = prod_base + blockIdx.y;
     const word* src;
     long long len;
+    int B = 16;
     if (desc) {
         const BatchDesc d = desc[prod];
         src = blockIdx.z ? src1 + d.boff : src0 + d.aoff;
         len = blockIdx.z ? d.nb : d.na;
+        if (TFT) B = tft_blocks(static_cast<long long>(d.na) + d.nb - 1);
     } else {
         len = blockIdx.z ? len1 : len0;
         src = (blockIdx.z ? src1 : src0) + prod * len;
+        if (TFT) B = beta;
     }
     const int rows = dcol_rows(len, c0 + v);
     const word* in = src + c0 + v;
@@ -99,11 +113,16 @@ k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long
             x[t] = word(0);
             if ((!ZHALF || t < 8) && row < rows) x[t] = in[static_cast<long long>(row) * kDLine];
         }
-        dif_regs<Ar, 16, ZHALF>(P.ar, x, P.rc);
+        if (TFT)
+            tdif16<Ar, ZHALF>(P.ar, x, P.rc, B);
+        else
+            dif_regs<Ar, 16, ZHALF>(P.ar, x, P.rc);
 #pragma unroll
-        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], ltab[j1 * 16 + t]);
+        for (int t = 1; t < 16; ++t)
+            if (!TFT || t < B) x[t] = P.ar.mulw(x[t], ltab[j1 * 16 + t]);
 #pragma unroll
-        for (int t = 0; t < 16; ++t) sm[(16 * t + j1) * kDCols + v] = x[t];
+        for (int t = 0; t < 16; ++t)
+            if (!TFT || t < B) sm[(16 * t + j1) * kDCols + v] = x[t];
     }
     __syncthreads();
     word* out = dst + prod * dst_stride + (blockIdx.z ? dst_off1 : 0) + c0 + v;
@@ -111,6 +130,7 @@ k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long
 #pragma unroll
     for (int i = 0; i < kDItems; ++i) {
         const int blk = g + kDGroups * i;
+        if (TFT && blk >= B) continue;
         word x[16];
 #pragma unroll
         for (int t = 0; t < 16; ++t) x[t] = sm[(16 * blk + t) * kDCols + v];
@@ -173,6 +193,7 @@ struct RowLayout {
 constexpr int kDRowsPerBlock = 4;      // rows of each operand per row block (64 threads)
 constexpr int kDRowMinBlocks32 = 20;   // 32-bit words: 20 blocks per SM (48 registers, no spills)
 constexpr int kDNttRowsPerBlock = 8;   // standalone row transforms (128 threads)
+constexpr int kDTftMaxBlocks = 13;     // uniform batches needing more row blocks run the full kernels
 
 __host__ __device__ constexpr size_t direct_row_smem_words() { return size_t(2 * kDRowsPerBlock) * RowLayout::kLine; }
 __host__ __device__ constexpr size_t direct_ntt_row_smem_words() { return size_t(kDNttRowsPerBlock) * RowLayout::kLine; }
@@ -181,9 +202,11 @@ __host__ __device__ constexpr size_t direct_ntt_row_smem_words() { return size_t
 // pointwise product (Montgomery), inverse row transforms of the product,
 // written over operand a in the workspace.  One thread per (row, j1); small
 // blocks keep the barrier-separated phases of neighbouring blocks apart.
-template <class Ar, int RPB>
+// TFT with descriptors: rows at or beyond the product's 16 B are not formed.
+template <class Ar, int RPB, bool TFT = false>
 __global__ void __launch_bounds__(RPB * 16, sizeof(typename Ar::word) == 4 ? kDRowMinBlocks32 : 1)
-k_row_polymul_d(DevPlan<Ar> P, typename Ar::word* __restrict__ ws, long long ws_stride, long long prod_base) {
+k_row_polymul_d(DevPlan<Ar> P, typename Ar::word* __restrict__ ws, long long ws_stride, long long prod_base,
+                const BatchDesc* __restrict__ desc) {
     using word = typename Ar::word;
     using tw = typename Ar::tw;
     using RL = RowLayout;
@@ -191,6 +214,10 @@ k_row_polymul_d(DevPlan<Ar> P, typename Ar::word* __restrict__ ws, long long ws_
     extern __shared__ __align__(16) unsigned char smraw[];
     word* sm = reinterpret_cast<word*>(smraw);
     const int r0 = blockIdx.x * RPB;
+    if (TFT && desc) {
+        const BatchDesc d = desc[prod_base + blockIdx.y];
+        if (r0 >= 16 * tft_blocks(static_cast<long long>(d.na) + d.nb - 1)) return;
+    }
     word* base = ws + (prod_base + blockIdx.y) * ws_stride;
     const int j1 = threadIdx.x & 15, r = threadIdx.x >> 4;
     // outer forward pass of row r of operand i (line RPB i + r)
@@ -289,11 +316,15 @@ k_row_ntt_d(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long prod_
 // Pass 3: inverse global twiddle (with n^-1 and the Montgomery factor folded
 // into itab), inverse column transforms, canonical cropped store of the first
 // out_len words of each product.
-template <class Ar>
+// TFT: the inverse of the truncated forward pass -- inner passes on the B
+// formed blocks, then per thread the inverse TFT of its 16-point outer pass
+// (B known outputs, known zero inputs above them), scaled like the other
+// unnormalised passes.
+template <class Ar, bool TFT = false>
 __global__ void __launch_bounds__(kDThreads)
 k_col_inv_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src, long long src_stride,
             typename Ar::word* __restrict__ dst, long long out_len, const typename Ar::tw* __restrict__ itab,
-            long long prod_base, const BatchDesc* __restrict__ desc) {
+            long long prod_base, const BatchDesc* __restrict__ desc, int beta, TftConsts<Ar> K) {
     using word = typename Ar::word;
     using tw = typename Ar::tw;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -303,9 +334,12 @@ k_col_inv_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src, long long 
     const long long prod = prod_base + blockIdx.y;
     const word* in = src + prod * src_stride + c0 + v;
     const tw* gt = itab + c0 + v;
+    int B = 16;
+    if (TFT) B = desc ? tft_blocks(static_cast<long long>(desc[prod].na) + desc[prod].nb - 1) : beta;
 #pragma unroll
     for (int i = 0; i < kDItems; ++i) {
         const int blk = g + kDGroups * i;
+        if (TFT && blk >= B) continue;
         word x[16];
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
@@ -333,10 +367,14 @@ k_col_inv_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src, long long 
         const int j1 = g + kDGroups * i;
         word x[16];
 #pragma unroll
-        for (int t = 0; t < 16; ++t) x[t] = sm[(16 * t + j1) * kDCols + v];
+        for (int t = 0; t < 16; ++t) x[t] = (!TFT || t < B) ? sm[(16 * t + j1) * kDCols + v] : word(0);
 #pragma unroll
-        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, ltab + j1 * 16 + t));
-        dit_regs<Ar, 16>(P.ar, x, P.rci);
+        for (int t = 1; t < 16; ++t)
+            if (!TFT || t < B) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, ltab + j1 * 16 + t));
+        if (TFT)
+            itft16_z16(P.ar, x, P.rc, P.rci, K, B);
+        else
+            dit_regs<Ar, 16>(P.ar, x, P.rci);
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
             const int row = 16 * t + j1;

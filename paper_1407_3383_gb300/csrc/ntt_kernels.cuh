@@ -741,6 +741,20 @@ static constexpr long long kMaxGridY = 65535;
 // c + t*(na+nb-1)) or uneven ones (desc: offsets and lengths per product,
 // a, b, c the flat buffers).  ws holds 2n words per product.
 template <class Ar>
+const TftConsts<Ar>& tft_consts(const ntt_plan* plan) {
+    if constexpr (std::is_same<Ar, Mont32>::value) return plan->tft32;
+    else if constexpr (std::is_same<Ar, Shoup64L>::value) return plan->tft64;
+    else return plan->tftf;
+}
+
+// The three direct 256 x 256 kernels (n = 2^16 above the one-block limit):
+// uniform batches (desc == null: product t at a + t*na, b + t*nb,
+// c + t*(na+nb-1)) or uneven ones (desc: offsets and lengths per product,
+// a, b, c the flat buffers).  ws holds 2n words per product.  Products
+// shorter than n take the truncated transforms (TFT) over the 16 B rows
+// their na + nb - 1 output words need; full-length uniform batches run the
+// plain kernels.
+template <class Ar>
 int launch_polymul_direct(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
                           long long na, const typename Ar::word* b, long long nb, long long batch,
                           typename Ar::word* c, typename Ar::word* ws, const BatchDesc* desc,
@@ -748,24 +762,32 @@ int launch_polymul_direct(const ntt_plan* plan, const DevPlan<Ar>& dp, const typ
     using word = typename Ar::word;
     constexpr long long N = 1LL << (2 * kDLog);
     const size_t smem_c = direct_col_smem_words() * sizeof(word);
-    const bool zhalf = !desc && 2 * std::max(na, nb) <= N;
-    auto kcf = zhalf ? k_col_fwd_d<Ar, true> : k_col_fwd_d<Ar, false>;
-    auto kci = k_col_inv_d<Ar>;
-    auto krp = k_row_polymul_d<Ar, kDRowsPerBlock>;
     const size_t smem_r = direct_row_smem_words() * sizeof(word);
+    const bool zhalf = !desc && 2 * std::max(na, nb) <= N;
+    // the truncated kernels pay off from 13 of the 16 row blocks down
+    // (measured: 14 blocks cost 1.01 of the full step, 12 blocks 0.90)
+    const int beta = desc ? 16 : tft_blocks(na + nb - 1);
+    const bool tft = desc != nullptr || beta <= kDTftMaxBlocks;
+    auto kcf = tft ? (zhalf ? k_col_fwd_d<Ar, true, true> : k_col_fwd_d<Ar, false, true>)
+                   : (zhalf ? k_col_fwd_d<Ar, true> : k_col_fwd_d<Ar, false>);
+    auto kci = tft ? k_col_inv_d<Ar, true> : k_col_inv_d<Ar>;
+    auto krp = tft ? k_row_polymul_d<Ar, kDRowsPerBlock, true> : k_row_polymul_d<Ar, kDRowsPerBlock>;
     if (allow_smem(kcf, smem_c) != cudaSuccess || allow_smem(kci, smem_c) != cudaSuccess ||
         allow_smem(krp, smem_r) != cudaSuccess)
         return check_launch("smem attr");
     const auto* itab = static_cast<const typename Ar::tw*>(plan->glob_inv_pm);
+    const unsigned row_blocks = static_cast<unsigned>(16 * (tft ? beta : 16) / kDRowsPerBlock);
     for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
-        kcf<<<dim3(kDLine / kDCols, nbat, 2), kDThreads, smem_c, st>>>(dp, a, na, b, nb, ws, 2 * N, N, p0, desc);
-        prof_mark(st, "k_col_fwd_d");
-        krp<<<dim3(kDLine / kDRowsPerBlock, nbat, 1), kDRowsPerBlock * 16, smem_r, st>>>(dp, ws, 2 * N, p0);
-        prof_mark(st, "k_row_polymul_d");
+        kcf<<<dim3(kDLine / kDCols, nbat, 2), kDThreads, smem_c, st>>>(dp, a, na, b, nb, ws, 2 * N, N, p0, desc,
+                                                                       tft ? beta : 16);
+        prof_mark(st, tft ? "k_col_fwd_d_tft" : "k_col_fwd_d");
+        krp<<<dim3(row_blocks, nbat, 1), kDRowsPerBlock * 16, smem_r, st>>>(dp, ws, 2 * N, p0, desc);
+        prof_mark(st, tft ? "k_row_polymul_d_tft" : "k_row_polymul_d");
         kci<<<dim3(kDLine / kDCols, nbat, 1), kDThreads, smem_c, st>>>(dp, ws, 2 * N, c, na + nb - 1,
-                                                                       itab, p0, desc);
-        prof_mark(st, "k_col_inv_d");
+                                                                       itab, p0, desc, tft ? beta : 16,
+                                                                       tft_consts<Ar>(plan));
+        prof_mark(st, tft ? "k_col_inv_d_tft" : "k_col_inv_d");
     }
     return check_launch("direct polymul passes");
 }
@@ -790,14 +812,15 @@ int launch_ntt_direct(const DevPlan<Ar>& dp, typename Ar::word* data, long long 
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
         const dim3 gc(kDLine / kDCols, nbat, 1), gr(kDLine / kDNttRowsPerBlock, nbat, 1);
         if (fwd) {
-            k_col_fwd_d<Ar, false><<<gc, kDThreads, smem_c, st>>>(dp, data, N, data, N, data, N, 0, p0, nullptr);
+            k_col_fwd_d<Ar, false><<<gc, kDThreads, smem_c, st>>>(dp, data, N, data, N, data, N, 0, p0, nullptr, 16);
             prof_mark(st, "k_col_fwd_d");
             krow<<<gr, kDNttRowsPerBlock * 16, smem_r, st>>>(dp, data, p0);
             prof_mark(st, "k_row_ntt_fwd_d");
         } else {
             krow<<<gr, kDNttRowsPerBlock * 16, smem_r, st>>>(dp, data, p0);
             prof_mark(st, "k_row_ntt_inv_d");
-            k_col_inv_d<Ar><<<gc, kDThreads, smem_c, st>>>(dp, data, N, data, N, dp.glob_inv, p0, nullptr);
+            k_col_inv_d<Ar><<<gc, kDThreads, smem_c, st>>>(dp, data, N, data, N, dp.glob_inv, p0, nullptr, 16,
+                                                           TftConsts<Ar>{});
             prof_mark(st, "k_col_inv_d");
         }
     }
@@ -996,7 +1019,7 @@ int launch_polymat(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename A
         for (long long p0 = 0; p0 < nn; p0 += kMaxGridY) {
             const unsigned nb = static_cast<unsigned>(std::min(nn - p0, kMaxGridY));
             kcf<<<dim3(kDLine / kDCols, nb, 2), kDThreads, smem_c, st>>>(dp, A, d, B, d, ws, NL, nn * NL, p0,
-                                                                        nullptr);
+                                                                        nullptr, 16);
             prof_mark(st, "k_col_fwd_d");
         }
         for (long long p0 = 0; p0 < 2 * nn; p0 += kMaxGridY) {
@@ -1049,7 +1072,8 @@ int launch_polymat(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename A
                 <<<dim3(kDLine / kDNttRowsPerBlock, nb, 1), kDNttRowsPerBlock * 16, smem_r, st>>>(dp, Ct, p0);
             prof_mark(st, "k_row_ntt_inv_d");
             k_col_inv_d<Ar><<<dim3(kDLine / kDCols, nb, 1), kDThreads, smem_c, st>>>(dp, Ct, NL, C, 2 * d - 1,
-                                                                                    dp.glob_inv, p0, nullptr);
+                                                                                    dp.glob_inv, p0, nullptr, 16,
+                                                                                    TftConsts<Ar>{});
             prof_mark(st, "k_col_inv_d");
         }
         return check_launch("polymat kernels");

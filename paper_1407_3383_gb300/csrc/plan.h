@@ -5,6 +5,7 @@
 #include <string>
 
 #include "engine.cuh"
+#include "tft.cuh"
 
 struct ntt_plan {
     uint64_t p = 0;
@@ -33,6 +34,10 @@ struct ntt_plan {
     gbntt::Tw32 r32{};                          // 2^32 rem p (undoes a Montgomery product)
     gbntt::Tw64 r64{};                          // 2^64 rem p
     gbntt::TwF inv_scalef{};                    // n^-1 (FP64 plans; no Montgomery factor)
+    // constants of the 16-point inverse TFT, per word policy
+    gbntt::TftConsts<gbntt::Mont32> tft32{};
+    gbntt::TftConsts<gbntt::Shoup64L> tft64{};
+    gbntt::TftConsts<gbntt::Fma50> tftf{};
 };
 
 // Three-prime integer product plan (intmul.cu): the primes, a transform plan

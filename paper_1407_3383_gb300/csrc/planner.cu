@@ -325,6 +325,29 @@ static void build_tables(ntt_plan* P, TableBuilder<TwT>& tb, Conv conv,
     }
 }
 
+// Constants of the 16-point inverse TFT (w = w_16 of the transform tables).
+template <class Ar, class Conv>
+static void build_tft(const ntt_plan* P, TftConsts<Ar>& K, Conv conv) {
+    const uint64_t p = P->p;
+    const uint64_t w16 = pow_mod(P->g, (p - 1) >> 4, p);
+    const uint64_t w16i = pow_mod(w16, p - 2, p);
+    const uint64_t inv2 = (p + 1) / 2;
+    const uint64_t inv8 = mul_mod(inv2, mul_mod(inv2, inv2, p), p);
+    uint64_t a = 1, b = 1;
+    for (int k = 0; k <= 4; ++k) {
+        K.inv2k[k] = conv(a);
+        K.pow2k[k] = conv(b);
+        a = mul_mod(a, inv2, p);
+        b = mul_mod(b, 2, p);
+    }
+    for (int e = 0; e < 8; ++e) {
+        const uint64_t we = pow_mod(w16, e, p), wie = pow_mod(w16i, e, p);
+        K.rci_half[e] = conv(mul_mod(wie, inv2, p));
+        K.rc_div8[e] = conv(mul_mod(we, inv8, p));
+        K.rci_mul8[e] = conv(mul_mod(wie, 8 % p, p));
+    }
+}
+
 template <class Ar, class TwT, class Conv>
 static int finish_plan(ntt_plan* P, DevPlan<Ar>& dp, Conv conv, uint64_t pm_factor) {
     TableBuilder<TwT> tb;
@@ -407,6 +430,7 @@ extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_p
         auto conv = [](uint64_t v) { return TwF{static_cast<double>(v)}; };
         rc = finish_plan<Fma50, TwF>(P, P->dpf, conv, 1);
         P->inv_scalef = conv(P->n_inv);
+        build_tft(P, P->tftf, conv);
     } else if (P->word_bytes == 4) {
         const uint32_t p32 = static_cast<uint32_t>(p);
         const uint32_t pinv = inv_pow2_32(p32);
@@ -416,6 +440,7 @@ extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_p
         P->inv_scale32 = conv(P->n_inv);
         P->pm_scale32 = conv(mul_mod(P->n_inv, (1ull << 32) % p, p));
         P->r32 = conv((1ull << 32) % p);
+        build_tft(P, P->tft32, conv);
     } else {
         const uint64_t pinv = inv_pow2_64(p);
         P->dp64.ar = Shoup64L{p, pinv};
@@ -425,6 +450,7 @@ extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_p
         P->inv_scale64 = conv(P->n_inv);
         P->pm_scale64 = conv(mul_mod(P->n_inv, r64, p));
         P->r64 = conv(r64);
+        build_tft(P, P->tft64, conv);
     }
     if (rc != NTT_OK) {
         if (P->d_tables) cudaFree(P->d_tables);

@@ -171,3 +171,30 @@ def test_direct_kernels_equal_generic_passes(p):
     assert (direct == generic).all()
     assert (direct[1] == O.polymul(p, a[1], b[1])).all()
 
+
+
+@pytest.mark.parametrize("p", [W.P_B, W.P1])
+@pytest.mark.parametrize("beta", list(range(1, 17)))
+def test_tft_products_every_length_class(p, beta):
+    """n = 2^16 products whose output needs B = beta of the 16 row blocks run
+    the truncated transforms (Section 5.1's TFT through Algorithm 1); they
+    must equal the padded generic passes word for word and the oracle."""
+    g = W.SplitMix64(0x7F7 + beta + p % 97)
+    L = 4096 * beta - (1 if beta % 2 else 2047)          # both ends of the class (13+ run full-length kernels)
+    na = (L + 1) // 2 + (beta % 3)                        # ragged, sometimes past n/2
+    nb = L + 1 - na
+    a = g.uniform_mod(p, 2 * na).reshape(2, na)
+    b = g.uniform_mod(p, 2 * nb).reshape(2, nb)
+    wb = 4 if p < (1 << 32) else 8
+    G.ntt_tune_reset()
+    tft = _polymul(p, 16, a, b)
+    try:
+        G.ntt_tune_import(f"{wb} 16 0 {5 if wb == 4 else 4} 4\n")
+        padded = _polymul(p, 16, a, b)
+    finally:
+        G.ntt_tune_reset()
+    assert (tft == padded).all()
+    if na * nb <= 1 << 24:
+        assert (tft[1] == O.polymul(p, a[1], b[1])).all()
+    else:
+        _sampled_check(p, a, b, tft, 24, beta)
