@@ -76,9 +76,9 @@ __device__ __forceinline__ int dcol_rows(long long len, long long c) {
 // Algorithm 1's rows, its outer 16-point pass truncated to B outputs.
 template <class Ar, bool ZHALF, bool TFT = false>
 __global__ void __launch_bounds__(kDThreads)
-k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long len0,
-            const typename Ar::word* __restrict__ src1, long long len1, typename Ar::word* __restrict__ dst,
-            long long dst_stride, long long dst_off1, long long prod_base,
+k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long len0, long long sstride0,
+            const typename Ar::word* __restrict__ src1, long long len1, long long sstride1,
+            typename Ar::word* __restrict__ dst, long long dst_stride, long long dst_off1, long long prod_base,
             const BatchDesc* __restrict__ desc, int beta) {
     using word = typename Ar::word;
     using tw = typename Ar::tw;
@@ -97,7 +97,7 @@ k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long
         if (TFT) B = tft_blocks(static_cast<long long>(d.na) + d.nb - 1);
     } else {
         len = blockIdx.z ? len1 : len0;
-        src = (blockIdx.z ? src1 : src0) + prod * len;
+        src = blockIdx.z ? src1 + prod * sstride1 : src0 + prod * sstride0;
         if (TFT) B = beta;
     }
     const int rows = dcol_rows(len, c0 + v);
@@ -323,8 +323,9 @@ k_row_ntt_d(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long prod_
 template <class Ar, bool TFT = false>
 __global__ void __launch_bounds__(kDThreads)
 k_col_inv_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src, long long src_stride,
-            typename Ar::word* __restrict__ dst, long long out_len, const typename Ar::tw* __restrict__ itab,
-            long long prod_base, const BatchDesc* __restrict__ desc, int beta, TftConsts<Ar> K) {
+            typename Ar::word* __restrict__ dst, long long out_len, long long dst_stride,
+            const typename Ar::tw* __restrict__ itab, long long prod_base, const BatchDesc* __restrict__ desc,
+            int beta, TftConsts<Ar> K) {
     using word = typename Ar::word;
     using tw = typename Ar::tw;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -357,7 +358,7 @@ k_col_inv_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src, long long 
         outp = dst + d.coff;
         out_len = static_cast<long long>(d.na) + d.nb - 1;
     } else {
-        outp = dst + prod * out_len;
+        outp = dst + prod * dst_stride;
     }
     const int rows = dcol_rows(out_len, c0 + v);
     word* o = outp + c0 + v;

@@ -26,6 +26,7 @@
 
 #include "../../include/gbntt.h"
 #include "direct.cuh"
+#include "subvec.cuh"
 #include "kernels.h"
 #include "plan.h"
 
@@ -779,17 +780,103 @@ int launch_polymul_direct(const ntt_plan* plan, const DevPlan<Ar>& dp, const typ
     const unsigned row_blocks = static_cast<unsigned>(16 * (tft ? beta : 16) / kDRowsPerBlock);
     for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
-        kcf<<<dim3(kDLine / kDCols, nbat, 2), kDThreads, smem_c, st>>>(dp, a, na, b, nb, ws, 2 * N, N, p0, desc,
-                                                                       tft ? beta : 16);
+        kcf<<<dim3(kDLine / kDCols, nbat, 2), kDThreads, smem_c, st>>>(dp, a, na, na, b, nb, nb, ws, 2 * N, N, p0,
+                                                                       desc, tft ? beta : 16);
         prof_mark(st, tft ? "k_col_fwd_d_tft" : "k_col_fwd_d");
         krp<<<dim3(row_blocks, nbat, 1), kDRowsPerBlock * 16, smem_r, st>>>(dp, ws, 2 * N, p0, desc);
         prof_mark(st, tft ? "k_row_polymul_d_tft" : "k_row_polymul_d");
         kci<<<dim3(kDLine / kDCols, nbat, 1), kDThreads, smem_c, st>>>(dp, ws, 2 * N, c, na + nb - 1,
-                                                                       itab, p0, desc, tft ? beta : 16,
-                                                                       tft_consts<Ar>(plan));
+                                                                       na + nb - 1, itab, p0, desc,
+                                                                       tft ? beta : 16, tft_consts<Ar>(plan));
         prof_mark(st, tft ? "k_col_inv_d_tft" : "k_col_inv_d");
     }
     return check_launch("direct polymul passes");
+}
+
+template <class Ar>
+const DevPlan<Ar>& devplan_of(const ntt_plan* plan) {
+    if constexpr (std::is_same<Ar, Mont32>::value) return plan->dp32;
+    else if constexpr (std::is_same<Ar, Shoup64L>::value) return plan->dp64;
+    else return plan->dpf;
+}
+
+template <class Ar, bool TFT>
+auto pre_kernel(int M) {
+    return M == 2 ? k_pre_fwd<Ar, 2, TFT> : M == 4 ? k_pre_fwd<Ar, 4, TFT> : M == 8 ? k_pre_fwd<Ar, 8, TFT>
+                                                                           : k_pre_fwd<Ar, 16, TFT>;
+}
+
+template <class Ar, bool TFT>
+auto post_kernel(int M) {
+    return M == 2 ? k_post_inv<Ar, 2, TFT> : M == 4 ? k_post_inv<Ar, 4, TFT> : M == 8 ? k_post_inv<Ar, 8, TFT>
+                                                                             : k_post_inv<Ar, 16, TFT>;
+}
+
+// The 2^16-point stage of a product of n = 2^17 .. 2^20 points: `count`
+// uniform sub-products at ws + s 2^17 (operand a) and + 2^16 (operand b),
+// transformed, multiplied and inverse-transformed in place by the child plan.
+template <class Ar>
+int launch_sub_products(const ntt_plan* core, typename Ar::word* ws, long long count, cudaStream_t st) {
+    using word = typename Ar::word;
+    const DevPlan<Ar>& dpc = devplan_of<Ar>(core);
+    constexpr long long S = 2 * kSubN;
+    const size_t smem_c = direct_col_smem_words() * sizeof(word);
+    const size_t smem_r = direct_row_smem_words() * sizeof(word);
+    auto kcf = k_col_fwd_d<Ar, false>;
+    auto krp = k_row_polymul_d<Ar, kDRowsPerBlock>;
+    auto kci = k_col_inv_d<Ar>;
+    if (allow_smem(kcf, smem_c) != cudaSuccess || allow_smem(kci, smem_c) != cudaSuccess ||
+        allow_smem(krp, smem_r) != cudaSuccess)
+        return check_launch("smem attr");
+    const auto* itab = static_cast<const typename Ar::tw*>(core->glob_inv_pm);
+    for (long long p0 = 0; p0 < count; p0 += kMaxGridY) {
+        const unsigned nb = static_cast<unsigned>(std::min(count - p0, kMaxGridY));
+        kcf<<<dim3(kDLine / kDCols, nb, 2), kDThreads, smem_c, st>>>(dpc, ws, kSubN, S, ws + kSubN, kSubN, S, ws,
+                                                                     S, kSubN, p0, nullptr, 16);
+        prof_mark(st, "k_col_fwd_d");
+        krp<<<dim3(kDLine / kDRowsPerBlock, nb, 1), kDRowsPerBlock * 16, smem_r, st>>>(dpc, ws, S, p0, nullptr);
+        prof_mark(st, "k_row_polymul_d");
+        kci<<<dim3(kDLine / kDCols, nb, 1), kDThreads, smem_c, st>>>(dpc, ws, S, ws, kSubN, S, itab, p0, nullptr,
+                                                                     16, TftConsts<Ar>{});
+        prof_mark(st, "k_col_inv_d");
+    }
+    return check_launch("sub-product passes");
+}
+
+// Products of n = 2^17 .. 2^20 points (Algorithm 1 with n1 = 2^16): the pass
+// across the rows, the 2^16-point stage on the rows, the inverse pass.
+// Uniform batches keep only lam = ceil((na + nb - 1) / 2^16) rows (TFT);
+// uneven ones (desc) keep all n2.
+template <class Ar>
+int launch_polymul_sub(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a, long long na,
+                       const typename Ar::word* b, long long nb, long long batch, typename Ar::word* c,
+                       typename Ar::word* ws, const BatchDesc* desc, cudaStream_t st) {
+    const int M = 1 << (static_cast<int>(plan->log2n) - kSubLog);
+    const long long L = na + nb - 1;
+    const int lam = desc ? M : static_cast<int>(std::min<long long>(M, (L + kSubN - 1) / kSubN));
+    const bool tft = !desc && lam < M;
+    const long long rows_stride = static_cast<long long>(lam) * 2 * kSubN;
+    const auto* pre = static_cast<const typename Ar::tw*>(plan->pre_fwd);
+    const auto* pre_inv = static_cast<const typename Ar::tw*>(plan->pre_inv);
+    prof_begin_call(st);
+    auto kpre = tft ? pre_kernel<Ar, true>(M) : pre_kernel<Ar, false>(M);
+    for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
+        const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
+        kpre<<<dim3(kSubN / kSubThreads, nbat, 2), kSubThreads, 0, st>>>(dp.ar, dp, a, na, na, b, nb, nb, ws,
+                                                                         rows_stride, 2 * kSubN, kSubN, pre, p0,
+                                                                         desc, lam);
+        prof_mark(st, "k_pre_fwd");
+    }
+    int rc = launch_sub_products<Ar>(plan->core, ws, batch * lam, st);
+    if (rc != NTT_OK) return rc;
+    auto kpost = tft ? post_kernel<Ar, true>(M) : post_kernel<Ar, false>(M);
+    for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
+        const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
+        kpost<<<dim3(kSubN / kSubThreads, nbat, 1), kSubThreads, 0, st>>>(
+            dp.ar, dp, tft_consts<Ar>(plan), ws, rows_stride, 2 * kSubN, c, L, L, pre_inv, p0, desc, lam);
+        prof_mark(st, "k_post_inv");
+    }
+    return check_launch("sub-vector passes");
 }
 
 // Standalone 2^16-point transforms of `batch` vectors in place with the
@@ -812,19 +899,54 @@ int launch_ntt_direct(const DevPlan<Ar>& dp, typename Ar::word* data, long long 
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
         const dim3 gc(kDLine / kDCols, nbat, 1), gr(kDLine / kDNttRowsPerBlock, nbat, 1);
         if (fwd) {
-            k_col_fwd_d<Ar, false><<<gc, kDThreads, smem_c, st>>>(dp, data, N, data, N, data, N, 0, p0, nullptr, 16);
+            k_col_fwd_d<Ar, false><<<gc, kDThreads, smem_c, st>>>(dp, data, N, N, data, N, N, data, N, 0, p0,
+                                                                  nullptr, 16);
             prof_mark(st, "k_col_fwd_d");
             krow<<<gr, kDNttRowsPerBlock * 16, smem_r, st>>>(dp, data, p0);
             prof_mark(st, "k_row_ntt_fwd_d");
         } else {
             krow<<<gr, kDNttRowsPerBlock * 16, smem_r, st>>>(dp, data, p0);
             prof_mark(st, "k_row_ntt_inv_d");
-            k_col_inv_d<Ar><<<gc, kDThreads, smem_c, st>>>(dp, data, N, data, N, dp.glob_inv, p0, nullptr, 16,
+            k_col_inv_d<Ar><<<gc, kDThreads, smem_c, st>>>(dp, data, N, data, N, N, dp.glob_inv, p0, nullptr, 16,
                                                            TftConsts<Ar>{});
             prof_mark(st, "k_col_inv_d");
         }
     }
     return check_launch("direct ntt passes");
+}
+
+// Standalone transforms of n = 2^17 .. 2^20 points in place (data 16-byte
+// aligned): forward = pass across the rows, then 2^16-point transforms of the
+// rows by the child plan; inverse = the reverse.
+template <class Ar>
+int launch_ntt_sub(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* data, long long batch,
+                   bool fwd, cudaStream_t st) {
+    const int M = 1 << (static_cast<int>(plan->log2n) - kSubLog);
+    const long long n = static_cast<long long>(M) * kSubN;
+    const DevPlan<Ar>& dpc = devplan_of<Ar>(plan->core);
+    int rc = NTT_OK;
+    if (!fwd) {
+        rc = launch_ntt_direct<Ar>(dpc, data, batch * M, false, st);
+        if (rc != NTT_OK) return rc;
+    }
+    prof_begin_call(st);
+    for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
+        const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
+        if (fwd) {
+            pre_kernel<Ar, false>(M)<<<dim3(kSubN / kSubThreads, nbat, 1), kSubThreads, 0, st>>>(
+                dp.ar, dp, data, n, n, data, n, n, data, n, kSubN, 0,
+                static_cast<const typename Ar::tw*>(plan->pre_fwd), p0, nullptr, M);
+            prof_mark(st, "k_pre_fwd");
+        } else {
+            post_kernel<Ar, false>(M)<<<dim3(kSubN / kSubThreads, nbat, 1), kSubThreads, 0, st>>>(
+                dp.ar, dp, TftConsts<Ar>{}, data, n, kSubN, data, n, n,
+                static_cast<const typename Ar::tw*>(plan->pre_inv), p0, nullptr, M);
+            prof_mark(st, "k_post_inv");
+        }
+    }
+    rc = check_launch("sub-vector pass");
+    if (rc != NTT_OK || !fwd) return rc;
+    return launch_ntt_direct<Ar>(dpc, data, batch * M, true, st);
 }
 
 template <class Ar>
@@ -851,7 +973,8 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
         }
         return check_launch("k_tile_polymul");
     }
-    if (cfg.logw == 0) return launch_polymul_direct<Ar>(plan, dp, a, na, b, nb, batch, c, ws, nullptr, st);
+    if (cfg.logw == 0 && k == 2 * kDLog) return launch_polymul_direct<Ar>(plan, dp, a, na, b, nb, batch, c, ws, nullptr, st);
+    if (cfg.logw == 0 && plan->core) return launch_polymul_sub<Ar>(plan, dp, a, na, b, nb, batch, c, ws, nullptr, st);
     const int k2 = plan->k2, k1 = plan->k1;
     const long long N = 1LL << k;
     const int logw = cfg.logw;
@@ -944,7 +1067,8 @@ int launch_batch_bucket(const ntt_plan* plan, const DevPlan<Ar>& dp, const typen
     using word = typename Ar::word;
     const int k = static_cast<int>(plan->log2n);
     const LaunchCfg cfg = launch_cfg(sizeof(word), k, plan->tile_max_log);
-    if (cfg.logw == 0) return launch_polymul_direct<Ar>(plan, dp, a, 0, b, 0, count, c, ws, d_desc, st);
+    if (cfg.logw == 0 && k == 2 * kDLog) return launch_polymul_direct<Ar>(plan, dp, a, 0, b, 0, count, c, ws, d_desc, st);
+    if (cfg.logw == 0 && plan->core) return launch_polymul_sub<Ar>(plan, dp, a, 0, b, 0, count, c, ws, d_desc, st);
     const int k2 = plan->k2, k1 = plan->k1;
     const long long N = 1LL << k;
     const int logw = cfg.logw, lrpc = cfg.lrpc;
@@ -1018,7 +1142,7 @@ int launch_polymat(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename A
             return check_launch("smem attr");
         for (long long p0 = 0; p0 < nn; p0 += kMaxGridY) {
             const unsigned nb = static_cast<unsigned>(std::min(nn - p0, kMaxGridY));
-            kcf<<<dim3(kDLine / kDCols, nb, 2), kDThreads, smem_c, st>>>(dp, A, d, B, d, ws, NL, nn * NL, p0,
+            kcf<<<dim3(kDLine / kDCols, nb, 2), kDThreads, smem_c, st>>>(dp, A, d, d, B, d, d, ws, NL, nn * NL, p0,
                                                                         nullptr, 16);
             prof_mark(st, "k_col_fwd_d");
         }
@@ -1072,8 +1196,8 @@ int launch_polymat(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename A
                 <<<dim3(kDLine / kDNttRowsPerBlock, nb, 1), kDNttRowsPerBlock * 16, smem_r, st>>>(dp, Ct, p0);
             prof_mark(st, "k_row_ntt_inv_d");
             k_col_inv_d<Ar><<<dim3(kDLine / kDCols, nb, 1), kDThreads, smem_c, st>>>(dp, Ct, NL, C, 2 * d - 1,
-                                                                                    dp.glob_inv, p0, nullptr, 16,
-                                                                                    TftConsts<Ar>{});
+                                                                                    2 * d - 1, dp.glob_inv, p0,
+                                                                                    nullptr, 16, TftConsts<Ar>{});
             prof_mark(st, "k_col_inv_d");
         }
         return check_launch("polymat kernels");
@@ -1105,7 +1229,10 @@ int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* d
     const long long N = 1LL << k;
     int logw = launch_cfg(sizeof(word), k, plan->tile_max_log).logw;
     if (logw == 0) {
-        if ((reinterpret_cast<uintptr_t>(data) & 15) == 0) return launch_ntt_direct<Ar>(dp, data, batch, fwd, st);
+        if ((reinterpret_cast<uintptr_t>(data) & 15) == 0) {
+            if (k == 2 * kDLog) return launch_ntt_direct<Ar>(dp, data, batch, fwd, st);
+            if (plan->core) return launch_ntt_sub<Ar>(plan, dp, data, batch, fwd, st);
+        }
         logw = generic_global_cfg(sizeof(word), k).logw;
     }
     const size_t smem_c = slab_words(slab_layout(k2, logw)) * sizeof(word);

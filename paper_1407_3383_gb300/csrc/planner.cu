@@ -388,6 +388,35 @@ static int finish_plan(ntt_plan* P, DevPlan<Ar>& dp, Conv conv, uint64_t pm_fact
     return NTT_OK;
 }
 
+// Tables of the pass across the n2 = n / 2^16 sub-vectors (n = 2^17 .. 2^20).
+template <class TwT, class Conv>
+static int build_pre_tables(ntt_plan* P, Conv conv) {
+    const uint64_t p = P->p;
+    const int m = static_cast<int>(P->log2n) - 16;
+    const uint64_t w = pow_mod(P->g, (p - 1) >> P->log2n, p);
+    const uint64_t wi = pow_mod(w, p - 2, p);
+    const uint64_t n2_inv = pow_mod((uint64_t(1) << m) % p, p - 2, p);
+    std::vector<uint64_t> vals;
+    std::vector<TwT> host(size_t(2) << P->log2n);
+    const size_t n = size_t(1) << P->log2n;
+    fill_outer_table(vals, p, w, m, 16);
+    for (size_t i = 0; i < n; ++i) host[i] = conv(vals[i]);
+    fill_outer_table(vals, p, wi, m, 16);
+    for (size_t i = 0; i < n; ++i) host[n + i] = conv(mul_mod(vals[i], n2_inv, p));
+    if (cudaMalloc(&P->d_pre, host.size() * sizeof(TwT)) != cudaSuccess) {
+        cudaGetLastError();
+        gbntt_set_error("cudaMalloc of the sub-vector tables failed");
+        return NTT_ERR_OOM;
+    }
+    if (cudaMemcpy(P->d_pre, host.data(), host.size() * sizeof(TwT), cudaMemcpyHostToDevice) != cudaSuccess) {
+        gbntt_set_error(std::string("table upload: ") + cudaGetErrorString(cudaGetLastError()));
+        return NTT_ERR_CUDA;
+    }
+    P->pre_fwd = P->d_pre;
+    P->pre_inv = static_cast<const TwT*>(P->d_pre) + n;
+    return NTT_OK;
+}
+
 extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_plan** out) {
     if (!out) return NTT_ERR_ARG;
     *out = nullptr;
@@ -452,7 +481,20 @@ extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_p
         P->r64 = conv(r64);
         build_tft(P, P->tft64, conv);
     }
+    if (rc == NTT_OK && log2n >= 17 && log2n <= 20) {
+        rc = ntt_plan_create(p, 16, flags & ~NTT_FLAG_PLAIN, &P->core);
+        if (rc == NTT_OK) {
+            if (flags & NTT_FLAG_FP64)
+                rc = build_pre_tables<TwF>(P, [](uint64_t v) { return TwF{static_cast<double>(v)}; });
+            else if (P->word_bytes == 4)
+                rc = build_pre_tables<Tw32>(P, [&](uint64_t v) { return tw32_of(v, static_cast<uint32_t>(p), P->dp32.ar.pinv); });
+            else
+                rc = build_pre_tables<Tw64>(P, [&](uint64_t v) { return tw64_of(v, p); });
+        }
+    }
     if (rc != NTT_OK) {
+        if (P->core) ntt_plan_destroy(P->core);
+        if (P->d_pre) cudaFree(P->d_pre);
         if (P->d_tables) cudaFree(P->d_tables);
         delete P;
         return rc;
@@ -463,6 +505,15 @@ extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_p
 
 extern "C" int ntt_plan_destroy(ntt_plan* plan) {
     if (!plan) return NTT_ERR_ARG;
+    if (plan->core) ntt_plan_destroy(plan->core);
+    if (plan->d_pre) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(plan->device);
+        cudaDeviceSynchronize();
+        cudaFree(plan->d_pre);
+        cudaSetDevice(cur);
+    }
     if (plan->d_tables) {
         int cur = 0;
         cudaGetDevice(&cur);

@@ -1,0 +1,110 @@
+// Transforms of n = 2^17 .. 2^20 points as Algorithm 1 with n1 = 2^16 and
+// n2 = n / 2^16 (Section 5.1): step 1 is an n2-point transform across the
+// sub-vectors, step 2 the twiddle w_n^(j1 [j2]), step 3 the 2^16-point
+// transforms of the n2 rows (the direct kernels of the plan's 2^16-point
+// child plan).  One thread owns column j1 of the n2 x 2^16 array and keeps
+// its n2 words in registers.
+//
+// Products take the TFT at this level too: a product of L output words
+// needs only lam = ceil(L / 2^16) of the n2 rows (step 1 truncated to lam
+// outputs, step 3 on lam rows, and the inverse TFT across the rows at the
+// end).  Rows go to the workspace interleaved -- row j2 of operand a at
+// (prod lam + j2) 2^17, of b 2^16 further -- so that the 2^16-point stage
+// sees a uniform batch of sub-products.
+#pragma once
+#include "direct.cuh"
+#include "tft.cuh"
+
+namespace gbntt {
+
+constexpr int kSubLog = 16;
+constexpr long long kSubN = 1LL << kSubLog;
+constexpr int kSubThreads = 256;
+
+// Steps 1 and 2: read rows j2 < M of every product's operand (zero beyond
+// its length), M-point DIF across them (truncated to lam outputs with TFT),
+// twiddle, and write row j2 < lam to dst + prod*dprod + j2*dsub (+ doff1 for
+// operand b, blockIdx.z = 1).  In place when dst is the source.
+template <class Ar, int M, bool TFT>
+__global__ void __launch_bounds__(kSubThreads)
+k_pre_fwd(Ar ar, DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long len0, long long sstride0,
+          const typename Ar::word* __restrict__ src1, long long len1, long long sstride1,
+          typename Ar::word* dst, long long dprod, long long dsub, long long doff1,
+          const typename Ar::tw* __restrict__ pre, long long prod_base, const BatchDesc* __restrict__ desc,
+          int lam) {
+    using word = typename Ar::word;
+    const long long j1 = static_cast<long long>(blockIdx.x) * kSubThreads + threadIdx.x;
+    const long long prod = prod_base + blockIdx.y;
+    const word* src;
+    long long len;
+    if (desc) {
+        const BatchDesc d = desc[prod];
+        src = blockIdx.z ? src1 + d.boff : src0 + d.aoff;
+        len = blockIdx.z ? d.nb : d.na;
+    } else {
+        src = blockIdx.z ? src1 + prod * sstride1 : src0 + prod * sstride0;
+        len = blockIdx.z ? len1 : len0;
+    }
+    word x[16];
+#pragma unroll
+    for (int j2 = 0; j2 < 16; ++j2) {
+        x[j2] = word(0);
+        if (j2 < M && j2 * kSubN + j1 < len) x[j2] = src[j2 * kSubN + j1];
+    }
+    if (TFT)
+        tdif<Ar, M, 0>(ar, x, P.rc, lam);
+    else
+        dif_sub<Ar, M, 0>(ar, x, P.rc);
+    word* out = dst + prod * dprod + (blockIdx.z ? doff1 : 0) + j1;
+#pragma unroll
+    for (int j2 = 0; j2 < M; ++j2)
+        if (!TFT || j2 < lam) out[j2 * dsub] = ar.mulw(x[j2], pre[j2 * kSubN + j1]);
+}
+
+// The inverse: rows j2 < lam of src + prod*sprod + j2*ssub, inverse twiddle
+// (with n2^-1 folded into pre_inv), inverse M-point transform across the
+// rows (the inverse TFT with zero inputs above lam, with TFT), canonical
+// store of the first out_len words at dst + prod*dprod (or the descriptor's
+// offset and length).
+template <class Ar, int M, bool TFT>
+__global__ void __launch_bounds__(kSubThreads)
+k_post_inv(Ar ar, DevPlan<Ar> P, TftConsts<Ar> K, const typename Ar::word* src, long long sprod, long long ssub,
+           typename Ar::word* dst, long long out_len, long long dprod, const typename Ar::tw* __restrict__ pre_inv,
+           long long prod_base, const BatchDesc* __restrict__ desc, int lam) {
+    using word = typename Ar::word;
+    const long long j1 = static_cast<long long>(blockIdx.x) * kSubThreads + threadIdx.x;
+    const long long prod = prod_base + blockIdx.y;
+    const word* in = src + prod * sprod + j1;
+    word x[16];
+#pragma unroll
+    for (int j2 = 0; j2 < 16; ++j2) {
+        x[j2] = word(0);
+        if (j2 < M && (!TFT || j2 < lam)) x[j2] = ar.mulw(in[j2 * ssub], pre_inv[j2 * kSubN + j1]);
+    }
+    if (TFT) {
+        // the inverse TFT returns 16 times its inputs, which pre_inv scaled
+        // by 1/M: multiply by M/16
+        itft_z<Ar, M, 0>(ar, x, P.rc, P.rci, K, lam);
+        if (M < 16) {
+#pragma unroll
+            for (int j2 = 0; j2 < M; ++j2) x[j2] = ar.mulw(x[j2], K.inv2k[4 - Log2<M>::v]);
+        }
+    } else {
+        dit_sub<Ar, M, 0>(ar, x, P.rci);
+    }
+    word* out;
+    long long len;
+    if (desc) {
+        const BatchDesc d = desc[prod];
+        out = dst + d.coff;
+        len = static_cast<long long>(d.na) + d.nb - 1;
+    } else {
+        out = dst + prod * dprod;
+        len = out_len;
+    }
+#pragma unroll
+    for (int j2 = 0; j2 < M; ++j2)
+        if (j2 * kSubN + j1 < len) out[j2 * kSubN + j1] = ar.canon(x[j2]);
+}
+
+}  // namespace gbntt

@@ -78,6 +78,31 @@ def test_uneven_batch_2e16_bucket(primes):
         assert (got[t] == want[t]).all(), t
 
 
+@pytest.mark.parametrize("primes", [[W.P1, W.P2], [W.P_B]])
+def test_uneven_batch_2e17_2e18_buckets(primes):
+    """Products of 2^17 and 2^18 points in one uneven batch (descriptor-driven
+    pass across 2^16-point rows): equal to the generic passes."""
+    g = W.SplitMix64(1718 + len(primes))
+    la = [40000, 70000, 33000, 100000, 131072]
+    lb = [40000, 20000, 33000, 90000, 1]
+    pidx = g.choice(len(primes), len(la))
+    a_list = [g.uniform_mod(primes[i], n) for i, n in zip(pidx, la)]
+    b_list = [g.uniform_mod(primes[i], n) for i, n in zip(pidx, lb)]
+    G.ntt_tune_reset()
+    got = _run_batch(primes, a_list, b_list, pidx)[0]
+    wb = 4 if primes[0] < (1 << 32) else 8
+    try:
+        G.ntt_tune_import("".join(f"{wb} {k} 0 {5 if wb == 4 else 4} 4\n" for k in (17, 18)))
+        padded = _run_batch(primes, a_list, b_list, pidx)[0]
+    finally:
+        G.ntt_tune_reset()
+    for t in range(len(la)):
+        assert (got[t] == padded[t]).all(), t
+        p = primes[pidx[t]]
+        for k in [0, got[t].size - 1, got[t].size // 3]:
+            assert int(got[t][k]) == O.poly_coeff(p, a_list[t], b_list[t], k)
+
+
 def test_config3_full_workload_sampled():
     """10,000 products, lengths log-uniform in [2^6, 2^18], each modulo one
     of three 62-bit primes: sampled coefficients and fingerprints."""

@@ -198,3 +198,37 @@ def test_tft_products_every_length_class(p, beta):
         assert (tft[1] == O.polymul(p, a[1], b[1])).all()
     else:
         _sampled_check(p, a, b, tft, 24, beta)
+
+
+def _generic_vs_default(p, log2n, a, b):
+    wb = 4 if p < (1 << 32) else 8
+    G.ntt_tune_reset()
+    got = _polymul(p, log2n, a, b)
+    k2 = log2n // 2
+    try:
+        G.ntt_tune_import(f"{wb} {log2n} 0 {5 if wb == 4 else 4} 4\n")
+        padded = _polymul(p, log2n, a, b)
+    finally:
+        G.ntt_tune_reset()
+    return got, padded
+
+
+@pytest.mark.parametrize("p,log2n,L", [
+    (W.P_B, 17, 65537), (W.P_B, 17, 131071),                        # n2 = 2: one row (TFT), both rows
+    (W.P1, 18, 65536), (W.P1, 18, 131073), (W.P1, 18, 196608), (W.P1, 18, 262143),   # every row count
+    (W.P_A, 19, 300001), (W.P2, 20, 70000), (W.P3, 20, 1048575),
+])
+def test_products_2e17_to_2e20(p, log2n, L):
+    """n = 2^17 .. 2^20: Algorithm 1 with 2^16-point rows (a pass across the
+    rows, the direct kernels on the rows, the inverse pass), truncated to the
+    rows the output needs; equal to the padded generic passes and the oracle
+    on sampled coefficients and fingerprints."""
+    g = W.SplitMix64(L + log2n)
+    na = (L + 1) // 2 + 17
+    nb = L + 1 - na
+    a = g.uniform_mod(p, na)[None, :]
+    b = g.uniform_mod(p, nb)[None, :]
+    got, padded = _generic_vs_default(p, log2n, a, b)
+    assert (got == padded).all()
+    _sampled_check(p, a, b, got, 32, L)
+

@@ -27,8 +27,8 @@ def test_default_shapes():
     # one-block sizes: 16 products per block for short vectors, 1 for tiles
     assert G.ntt_tune_get(4, 8)[0] == 4
     assert G.ntt_tune_get(8, 12)[0] == 0
-    # n = 2^16 above the one-block limit: the direct 256 x 256 kernels (logw = 0)
-    assert G.ntt_tune_get(4, 16)[1] == 0
-    assert G.ntt_tune_get(8, 16)[1] == 0
-    assert G.ntt_tune_get(4, 17)[1] >= 1
+    # n = 2^16 .. 2^20 above the one-block limit: the direct kernels (logw = 0)
+    for k in range(16, 21):
+        assert G.ntt_tune_get(4, k)[1] == 0 and G.ntt_tune_get(8, k)[1] == 0
+    assert G.ntt_tune_get(4, 21)[1] >= 1 and G.ntt_tune_get(4, 15)[1] >= 1
 
