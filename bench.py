@@ -541,7 +541,7 @@ def run_serve(args, world, rank, local):
         span = time.perf_counter() - start
         return np.array(lat), span
 
-    stream(np.zeros(min(4, len(reqs))))                   # warm-up
+    stream(np.zeros(len(reqs)))                           # warm-up: every size class launched once
     lat, span = stream(np.zeros(len(reqs)))                # closed loop: all at once
     sat = len(reqs) / span
     runs = [{"load": "closed", "products_per_s": sat, "p50_ms": float(np.percentile(lat, 50)),
