@@ -756,29 +756,32 @@ def run_tft(args, world, rank, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
-    p, batch = W.P_B, 256
+    batch = 256
     g = W.SplitMix64(W.SEED_BASE + 51)
-    rows = []
-    with G.Plan(p, 16) as plan:
-        ws = G.alloc_workspace(plan, batch)
-        for beta in [16, 14, 12, 10, 8, 6, 4, 2, 1]:
-            na = nb = 2048 * beta
-            a = torch.from_numpy(g.uniform_mod(p, batch * na).astype(np.uint32)).to(dev)
-            b = torch.from_numpy(g.uniform_mod(p, batch * nb).astype(np.uint32)).to(dev)
-            c = torch.empty(batch * (na + nb - 1), dtype=torch.uint32, device=dev)
-            step = lambda: G.polymul_mod_p_batch(plan, a, na, b, nb, batch, c, G.NTT_SCHED_FUSED, ws,
-                                                 stream=stream)
-            for _ in range(3):
-                step()
-            torch.cuda.synchronize()
-            ms = statistics.median(timed_steps(step, lambda: flush_buf.fill_(1), 20, stream))
-            rows.append({"blocks": beta, "na": na, "nb": nb, "ms": ms, "products_per_s": batch / (ms * 1e-3)})
-    full = rows[0]["ms"]
-    for r in rows:
-        r["time_vs_padded"] = r["ms"] / full
-    if rank == 0:
-        print(json.dumps({"metric": "2^16-point products by output length (truncated transforms)",
-                          "p": p, "batch": batch, "n_gpus": world, "rows": rows}), flush=True)
+    for p, dt in [(W.P_B, np.uint32), (W.P1, np.uint64)]:
+        rows = []
+        with G.Plan(p, 16) as plan:
+            ws = G.alloc_workspace(plan, batch)
+            for beta in [16, 14, 13, 12, 11, 10, 8, 6, 4, 2, 1]:
+                na = nb = 2048 * beta
+                a = torch.from_numpy(g.uniform_mod(p, batch * na).astype(dt)).to(dev)
+                b = torch.from_numpy(g.uniform_mod(p, batch * nb).astype(dt)).to(dev)
+                c = torch.empty(batch * (na + nb - 1), dtype=a.dtype, device=dev)
+                step = lambda: G.polymul_mod_p_batch(plan, a, na, b, nb, batch, c, G.NTT_SCHED_FUSED, ws,
+                                                     stream=stream)
+                for _ in range(3):
+                    step()
+                torch.cuda.synchronize()
+                ms = statistics.median(timed_steps(step, lambda: flush_buf.fill_(1), 20, stream))
+                rows.append({"blocks": beta, "na": na, "nb": nb, "ms": ms,
+                             "products_per_s": batch / (ms * 1e-3)})
+                del a, b, c
+        full = rows[0]["ms"]
+        for r in rows:
+            r["time_vs_padded"] = r["ms"] / full
+        if rank == 0:
+            print(json.dumps({"metric": "2^16-point products by output length (truncated transforms)",
+                              "p": p, "batch": batch, "n_gpus": world, "rows": rows}), flush=True)
 
 
 def main():

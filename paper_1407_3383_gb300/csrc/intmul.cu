@@ -1,22 +1,29 @@
 // Integer product by Kronecker segmentation and the three-prime transform
 // (Section 5.3).
 //
-// a and b (little-endian 32-bit limbs) are cut into chunks of h = 64 bits,
-// giving polynomials A, B with A(2^64) = a, B(2^64) = b and d = ceil(n/2)
-// coefficients.  Each coefficient of C = A B is below d 2^128 <= 2^150, far
-// below P1 P2 P3 ~ 2^183 for the three primes P_i = k_i 2^40 + 1 of the
-// 62-bit window, so C is recovered exactly from C mod P1, P2, P3 (computed
-// as three polynomial products over Z/P_iZ, Section 5.2) by Garner's mixed-
-// radix Chinese remaindering:
+// a and b (little-endian 32-bit limbs) are cut into chunks of h bits, giving
+// polynomials A, B with A(2^h) = a, B(2^h) = b.  h is the paper's choice:
+// the largest h (here at most 96) for which every coefficient of C = A B,
+// a sum of at most m = min(da, db) products of h-bit chunks, stays below
+// 2^H with H = 2 h + bitlength(m) <= 183 < log2(P1 P2 P3) for the three
+// primes P_i = k_i 2^40 + 1 of the 62-bit window -- so the number d of
+// chunks is minimal (80 to 90 bits at the sizes served).  C is recovered
+// exactly from C mod P1, P2, P3 (three polynomial products over Z/P_iZ,
+// Section 5.2) by Garner's mixed-radix Chinese remaindering:
 //     x1 = r1,  x2 = (r2 - x1) P1^-1 mod P2,
 //     x3 = ((r3 - x1) P1^-1 - x2) P2^-1 mod P3,
 //     c  = x1 + P1 (x2 + P2 x3)          (exact, < P1 P2 P3).
-// Finally c(2^64) is evaluated: coefficient k lands at bit 64 k and the
-// overlapping words are summed with carry propagation, done as a parallel
-// scan of (generate, propagate, kill) carry states over 64-bit words.
+// Finally C(2^h) is evaluated: coefficient k (three words) lands at bit h k,
+// each 64-bit word of the result sums the slices of the (at most four)
+// coefficients overlapping it, and carries are propagated by a parallel scan
+// of (generate, propagate, kill) states over the words.  The integer matrix
+// product keeps h = 64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -42,7 +49,25 @@ __device__ __forceinline__ uint8_t carry_combine(uint8_t before, uint8_t after) 
 struct CrtArgs {
     uint64_t P1, P2, P3;
     Tw64 inv12, inv13, inv23;
+    Tw64 r64[3];   // 2^64 rem P_i (chunks wider than 64 bits)
 };
+
+// Chunk k of h bits (64 <= h <= 96) of a limb array of n limbs: bits
+// [k h, k h + h), from at most four limbs, as (low 64 bits, high part).
+__device__ __forceinline__ void chunk_bits(const uint32_t* x, long long n, long long k, int h, uint64_t& lo,
+                                           uint64_t& hi) {
+    const long long b0 = k * h;
+    const long long i0 = b0 >> 5;
+    const int r = static_cast<int>(b0 & 31);
+    u128 v = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (i0 + q < n) v |= static_cast<u128>(x[i0 + q]) << (32 * q);
+    v >>= r;
+    v &= (static_cast<u128>(1) << h) - 1;
+    lo = static_cast<uint64_t>(v);
+    hi = static_cast<uint64_t>(v >> 64);
+}
 
 // chunk k of a limb array (two limbs, the high one may be past the end)
 __device__ __forceinline__ uint64_t chunk_of(const uint32_t* x, long long n, long long k) {
@@ -59,17 +84,25 @@ __device__ __forceinline__ uint64_t reduce_chunk(uint64_t x, uint64_t P) {
     return (x >= P) ? x - P : x;
 }
 
-// Operand chunks reduced modulo each prime: red[i][0 .. da) = a, red[i][da .. da+db) = b.
+// Operand chunks of h bits reduced modulo each prime: red[i][0 .. da) = a,
+// red[i][da .. da+db) = b.  A chunk lo + 2^64 hi is hi (2^64 rem P) + lo.
 __global__ void k_split(const uint32_t* __restrict__ a, long long na, const uint32_t* __restrict__ b,
-                        long long nb, long long da, long long db, uint64_t* __restrict__ red,
+                        long long nb, long long da, long long db, int h, uint64_t* __restrict__ red,
                         long long red_stride, CrtArgs C) {
     const long long total = da + db;
+    const uint64_t P[3] = {C.P1, C.P2, C.P3};
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
          k += (long long)gridDim.x * blockDim.x) {
-        const uint64_t ch = (k < da) ? chunk_of(a, na, k) : chunk_of(b, nb, k - da);
-        red[k] = reduce_chunk(ch, C.P1);
-        red[red_stride + k] = reduce_chunk(ch, C.P2);
-        red[2 * red_stride + k] = reduce_chunk(ch, C.P3);
+        uint64_t lo, hi;
+        if (k < da)
+            chunk_bits(a, na, k, h, lo, hi);
+        else
+            chunk_bits(b, nb, k - da, h, lo, hi);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const Shoup64 A{P[i], 0};
+            red[i * red_stride + k] = A.add(A.mulw(hi, C.r64[i]), reduce_chunk(lo, P[i]));
+        }
     }
 }
 
@@ -111,23 +144,39 @@ __global__ void k_crt(const uint64_t* __restrict__ r, long long r_stride, long l
     }
 }
 
-// Word j of sum_k c_k 2^(64 k) before carries: S_j = w0(c_j) + w1(c_{j-1}) + w2(c_{j-2})
-// as (low word, high part <= 2).
-__device__ __forceinline__ void column_sum(const uint64_t* W, long long nc, long long j, uint64_t& lo,
+// Bits [off, off + 64) of the 192-bit value c = (w0, w1, w2) (off may be
+// negative: the slice then starts below c's first bit).
+__device__ __forceinline__ uint64_t slice64(const uint64_t* w, long long off) {
+    if (off <= -64 || off >= 192) return 0;
+    if (off < 0) return w[0] << (-off);
+    const int q = static_cast<int>(off >> 6), r = static_cast<int>(off & 63);
+    const uint64_t a = w[q];
+    const uint64_t b = (q + 1 < 3) ? w[q + 1] : 0;
+    return r ? (a >> r) | (b << (64 - r)) : a;
+}
+
+// Word j of sum_k c_k 2^(h k) before carries: the 64-bit slices of the
+// coefficients overlapping bits [64 j, 64 j + 64), as (low word, high part
+// <= 3).  With h = 64 these are w0(c_j) + w1(c_{j-1}) + w2(c_{j-2}).
+__device__ __forceinline__ void column_sum(const uint64_t* W, long long nc, long long j, int h, uint64_t& lo,
                                            uint64_t& hi) {
     u128 s = 0;
-    if (j >= 0 && j < nc) s += W[3 * j];
-    if (j - 1 >= 0 && j - 1 < nc) s += W[3 * (j - 1) + 1];
-    if (j - 2 >= 0 && j - 2 < nc) s += W[3 * (j - 2) + 2];
+    if (j >= 0) {
+        const long long top = 64 * j + 63;
+        long long k = (64 * j - 191 + h - 1) / h;   // first k with h k + 192 > 64 j
+        if (64 * j - 191 <= 0) k = 0;
+        const long long k1 = std::min(nc - 1, top / h);
+        for (; k <= k1; ++k) s += slice64(W + 3 * k, 64 * j - h * k);
+    }
     lo = static_cast<uint64_t>(s);
     hi = static_cast<uint64_t>(s >> 64);
 }
 
 // u_j = lo_j + hi_{j-1}: its low word v_j and its carry state.
-__device__ __forceinline__ uint8_t word_state(const uint64_t* W, long long nc, long long j, uint64_t& v) {
+__device__ __forceinline__ uint8_t word_state(const uint64_t* W, long long nc, long long j, int h, uint64_t& v) {
     uint64_t lo, hi, plo, phi;
-    column_sum(W, nc, j, lo, hi);
-    column_sum(W, nc, j - 1, plo, phi);
+    column_sum(W, nc, j, h, lo, hi);
+    column_sum(W, nc, j - 1, h, plo, phi);
     const u128 u = static_cast<u128>(lo) + phi;
     v = static_cast<uint64_t>(u);
     if (u >> 64) return kGen;
@@ -143,7 +192,7 @@ __device__ __forceinline__ void store_word(uint32_t* c, long long nlimbs, long l
 // relative to the start of its block (stored into st); per block the state
 // of the whole block (agg).
 __global__ void __launch_bounds__(kCarryThreads)
-k_carry_local(const uint64_t* __restrict__ W, long long nc, long long nwords, uint32_t* __restrict__ c,
+k_carry_local(const uint64_t* __restrict__ W, long long nc, long long nwords, int h, uint32_t* __restrict__ c,
               long long nlimbs, uint8_t* __restrict__ st, uint8_t* __restrict__ agg, long long nblocks) {
     __shared__ uint8_t warp_tot[kCarryThreads / 32];
     // entry blockIdx.y of a batch of integers laid out back to back
@@ -159,7 +208,7 @@ k_carry_local(const uint64_t* __restrict__ W, long long nc, long long nwords, ui
         uint64_t v = 0;
         s[e] = kKill;
         if (j < nwords) {
-            s[e] = word_state(W, nc, j, v);
+            s[e] = word_state(W, nc, j, h, v);
             store_word(c, nlimbs, j, v);
         }
         tot = carry_combine(tot, s[e]);
@@ -233,19 +282,37 @@ int grid_of(long long n, int threads) {
 }
 
 struct Layout {
-    int log2n;
+    int log2n, h;
     long long da, db, nc, nwords, nblocks;
-    size_t off_red, off_res, off_W, off_st, off_agg, off_poly, total;
+    size_t off_red, off_res, off_W, off_st, off_agg, off_poly, poly_bytes, total;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
+int bit_length(long long m) {
+    int b = 0;
+    while (m > 0) ++b, m >>= 1;
+    return b;
+}
+
+// Section 5.3's chunk size: the largest h (64 <= h <= 96) with
+// 2 h + bitlength(min(da, db)) <= 183, da, db the chunk counts of a and b.
+int chunk_bits_for(size_t na, size_t nb) {
+    for (int h = 96; h > 64; --h) {
+        const long long da = static_cast<long long>((32 * na + h - 1) / h);
+        const long long db = static_cast<long long>((32 * nb + h - 1) / h);
+        if (2 * h + bit_length(std::min(da, db)) <= 183) return h;
+    }
+    return 64;
+}
+
 Layout layout_of(const intmul_plan* P, size_t na, size_t nb) {
     Layout L{};
-    L.da = static_cast<long long>((na + 1) / 2);
-    L.db = static_cast<long long>((nb + 1) / 2);
+    L.h = chunk_bits_for(na, nb);
+    L.da = static_cast<long long>((32 * na + L.h - 1) / L.h);
+    L.db = static_cast<long long>((32 * nb + L.h - 1) / L.h);
     L.nc = L.da + L.db - 1;
-    L.nwords = L.da + L.db;
+    L.nwords = static_cast<long long>((na + nb + 1) / 2);
     L.nblocks = (L.nwords + kCarryBlock - 1) / kCarryBlock;
     int k = 1;
     while ((1LL << k) < L.nc) ++k;
@@ -264,9 +331,32 @@ Layout layout_of(const intmul_plan* P, size_t na, size_t nb) {
     L.off_poly = off;
     size_t poly = 0;
     if (k <= static_cast<int>(P->max_log2n) && P->plans[0][k])
-        poly = polymul_ws_bytes(P->plans[0][k], 1, NTT_SCHED_FUSED);
-    L.total = align256(off + poly);
+        poly = align256(polymul_ws_bytes(P->plans[0][k], 1, NTT_SCHED_FUSED));
+    L.poly_bytes = poly;
+    L.total = align256(off + 3 * poly);                 // one product workspace per prime
     return L;
+}
+
+// Helper streams of an intmul plan: the three primes' products run
+// concurrently, the second and third on two streams forked from the
+// caller's stream (one pair per caller stream) and joined back by events.
+struct Helpers {
+    std::mutex mu;
+    std::map<cudaStream_t, std::array<cudaStream_t, 2>> by_stream;
+};
+
+int helper_streams(const intmul_plan* P, cudaStream_t st, std::array<cudaStream_t, 2>& out) {
+    Helpers* H = static_cast<Helpers*>(P->helpers);
+    std::lock_guard<std::mutex> lock(H->mu);
+    auto it = H->by_stream.find(st);
+    if (it == H->by_stream.end()) {
+        std::array<cudaStream_t, 2> s{};
+        for (auto& x : s)
+            if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) return NTT_ERR_CUDA;
+        it = H->by_stream.emplace(st, s).first;
+    }
+    out = it->second;
+    return NTT_OK;
 }
 
 }  // namespace
@@ -289,6 +379,11 @@ extern "C" int intmul_plan_create(size_t max_limbs, intmul_plan** out) {
     if (!P) return NTT_ERR_OOM;
     cudaGetDevice(&P->device);
     P->max_log2n = static_cast<unsigned>(kmax);
+    P->helpers = new (std::nothrow) Helpers();
+    if (!P->helpers) {
+        delete P;
+        return NTT_ERR_OOM;
+    }
     for (int i = 0; i < 3; ++i) {
         int rc = ntt_find_prime(62, 40, static_cast<unsigned>(i), &P->P[i]);
         if (rc != NTT_OK) {
@@ -303,6 +398,7 @@ extern "C" int intmul_plan_create(size_t max_limbs, intmul_plan** out) {
                 for (int a = 0; a < 3; ++a)
                     for (int b = 1; b <= kmax; ++b)
                         if (P->plans[a][b]) ntt_plan_destroy(P->plans[a][b]);
+                delete static_cast<Helpers*>(P->helpers);
                 delete P;
                 return rc;
             }
@@ -311,12 +407,22 @@ extern "C" int intmul_plan_create(size_t max_limbs, intmul_plan** out) {
     P->inv12 = host::tw64_of(inv(P->P[0], P->P[1]), P->P[1]);
     P->inv13 = host::tw64_of(inv(P->P[0], P->P[2]), P->P[2]);
     P->inv23 = host::tw64_of(inv(P->P[1], P->P[2]), P->P[2]);
+    for (int i = 0; i < 3; ++i)
+        P->r64[i] = host::tw64_of(static_cast<uint64_t>((static_cast<u128>(1) << 64) % P->P[i]), P->P[i]);
     *out = P;
     return NTT_OK;
 }
 
 extern "C" int intmul_plan_destroy(intmul_plan* plan) {
     if (!plan) return NTT_ERR_ARG;
+    if (Helpers* H = static_cast<Helpers*>(plan->helpers)) {
+        for (auto& kv : H->by_stream)
+            for (cudaStream_t x : kv.second) {
+                cudaStreamSynchronize(x);
+                cudaStreamDestroy(x);
+            }
+        delete H;
+    }
     for (int i = 0; i < 3; ++i)
         for (int k = 1; k <= 24; ++k)
             if (plan->plans[i][k]) ntt_plan_destroy(plan->plans[i][k]);
@@ -350,25 +456,45 @@ extern "C" int intmul_crt(const intmul_plan* plan, const uint32_t* d_a, size_t n
     uint8_t* sst = ws + L.off_st;
     uint8_t* agg = ws + L.off_agg;
     uint64_t* poly = reinterpret_cast<uint64_t*>(ws + L.off_poly);
-    CrtArgs C{plan->P[0], plan->P[1], plan->P[2], plan->inv12, plan->inv13, plan->inv23};
+    CrtArgs C{plan->P[0], plan->P[1], plan->P[2], plan->inv12, plan->inv13, plan->inv23,
+              {plan->r64[0], plan->r64[1], plan->r64[2]}};
     const long long red_stride = L.da + L.db;
 
     prof_begin_call(st);
     k_split<<<grid_of(red_stride, 256), 256, 0, st>>>(d_a, static_cast<long long>(na), d_b,
-                                                       static_cast<long long>(nb), L.da, L.db, red,
+                                                       static_cast<long long>(nb), L.da, L.db, L.h, red,
                                                        red_stride, C);
     prof_mark(st, "k_split");
+    // the three residue products concurrently: prime 1 on the caller's
+    // stream, primes 2 and 3 on its helper streams
+    std::array<cudaStream_t, 2> hs{};
+    int rc = helper_streams(plan, st, hs);
+    if (rc != NTT_OK) return rc;
+    cudaEvent_t ev[3];
+    for (auto& e : ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return NTT_ERR_CUDA;
+    cudaEventRecord(ev[0], st);
+    const cudaStream_t sp[3] = {st, hs[0], hs[1]};
     for (int i = 0; i < 3; ++i) {
+        if (i) cudaStreamWaitEvent(sp[i], ev[0], 0);
         const ntt_plan* np = plan->plans[i][L.log2n];
-        int rc = launch_polymul_fused<Shoup64L>(np, np->dp64, red + i * red_stride, L.da,
-                                               red + i * red_stride + L.da, L.db, 1, res + i * L.nc,
-                                               poly, np->pm_scale64, st);
-        if (rc != NTT_OK) return rc;
+        rc = launch_polymul_fused<Shoup64L>(np, np->dp64, red + i * red_stride, L.da, red + i * red_stride + L.da,
+                                            L.db, 1, res + i * L.nc,
+                                            reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(poly) +
+                                                                        i * L.poly_bytes),
+                                            np->pm_scale64, sp[i]);
+        if (rc != NTT_OK) break;
+        if (i) {
+            cudaEventRecord(ev[i], sp[i]);
+            cudaStreamWaitEvent(st, ev[i], 0);
+        }
     }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (rc != NTT_OK) return rc;
     k_crt<<<grid_of(L.nc, 256), 256, 0, st>>>(res, L.nc, L.nc, W, C);
     prof_mark(st, "k_crt");
     k_carry_local<<<static_cast<unsigned>(L.nblocks), kCarryThreads, 0, st>>>(
-        W, L.nc, L.nwords, d_c, static_cast<long long>(na + nb), sst, agg, L.nblocks);
+        W, L.nc, L.nwords, L.h, d_c, static_cast<long long>(na + nb), sst, agg, L.nblocks);
     prof_mark(st, "k_carry_local");
     k_carry_blocks<<<1, 1024, 0, st>>>(agg, L.nblocks);
     prof_mark(st, "k_carry_blocks");
@@ -453,7 +579,8 @@ extern "C" int intmat_mul(const intmul_plan* plan, const uint32_t* d_A, size_t n
     uint8_t* sst = ws + L.off_st;
     uint8_t* agg = ws + L.off_agg;
     uint64_t* poly = reinterpret_cast<uint64_t*>(ws + L.off_poly);
-    CrtArgs C{plan->P[0], plan->P[1], plan->P[2], plan->inv12, plan->inv13, plan->inv23};
+    CrtArgs C{plan->P[0], plan->P[1], plan->P[2], plan->inv12, plan->inv13, plan->inv23,
+              {plan->r64[0], plan->r64[1], plan->r64[2]}};
     const long long red_stride = 2 * L.nn * L.d;
     const long long nlimbs = static_cast<long long>(na + nb + 1);
     prof_begin_call(st);
@@ -472,7 +599,7 @@ extern "C" int intmat_mul(const intmul_plan* plan, const uint32_t* d_A, size_t n
     prof_mark(st, "k_crt");
     const unsigned ny = static_cast<unsigned>(L.nn);
     k_carry_local<<<dim3(static_cast<unsigned>(L.nblocks), ny), kCarryThreads, 0, st>>>(
-        W, L.nc, L.nwords, d_C, nlimbs, sst, agg, L.nblocks);
+        W, L.nc, L.nwords, 64, d_C, nlimbs, sst, agg, L.nblocks);
     prof_mark(st, "k_carry_local");
     k_carry_blocks<<<ny, 1024, 0, st>>>(agg, L.nblocks);
     prof_mark(st, "k_carry_blocks");

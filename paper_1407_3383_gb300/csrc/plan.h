@@ -56,6 +56,8 @@ struct intmul_plan {
     uint64_t P[3] = {0, 0, 0};
     ntt_plan* plans[3][25] = {};
     gbntt::Tw64 inv12{}, inv13{}, inv23{};   // P1^-1 mod P2, P1^-1 mod P3, P2^-1 mod P3
+    gbntt::Tw64 r64[3]{};                    // 2^64 mod P_i
+    void* helpers = nullptr;                 // per caller stream: two streams for primes 2 and 3
 };
 
 namespace gbntt {
