@@ -688,9 +688,15 @@ def run_suite(args, world, rank, local):
         step = lambda: G.polymat_mul(plan, A, B, n, d, C, ws, stream=stream)
         ms = med(step, 10)
         per, _ = profile_window(G, step, flush, 3)
+        freq_ms = statistics.mean(per.get("k_polymat_freq", [ms]))
+        macs = n ** 3 * (1 << 16) / (freq_ms * 1e-3)
+        imad_peak = SM_COUNT * 64 * 2.07e9              # one 32-bit multiply-add pipe: 64 lanes per SM
         emit("polynomial matrix product 32 x 32, degree < 2^15, mod 469762049 (u32)", ms=ms,
              kernels_ms={k: statistics.mean(v) for k, v in per.items()},
-             freq_mulmod_per_s=n ** 3 * (1 << 16) / (statistics.mean(per.get("k_polymat_freq", [ms])) * 1e-3))
+             freq_mulmod_per_s=macs,
+             freq_roofline={"bound": "alu (wide multiply-add pipe)", "achieved": macs, "peak": imad_peak,
+                            "frac": macs / imad_peak, "unit": "multiply-adds/s",
+                            "peak_basis": "152 SMs x 64 lanes x 2070 MHz; one wide multiply-add per term"})
         del A, B, C, ws
 
     # integer matrix product, n = 32, entries of 2^15 limbs (Table 17's shape)
