@@ -211,7 +211,8 @@ def make_inputs():
     return p, a, b
 
 
-KERNEL_SOURCES = ["engine.cuh", "modarith.cuh", "direct.cuh", "ntt_kernels.cuh", "ntt_u32.cu", "ntt_u64.cu"]
+KERNEL_SOURCES = ["engine.cuh", "modarith.cuh", "tft.cuh", "direct.cuh", "subvec.cuh", "ntt_kernels.cuh",
+                  "ntt_u32.cu", "ntt_u64.cu"]
 
 
 def source_hash() -> str:
