@@ -812,6 +812,18 @@ auto post_kernel(int M) {
                                                                              : k_post_inv<Ar, 16, TFT>;
 }
 
+template <class Ar, bool ZHALF, bool TFT>
+auto colx_fwd_kernel(int C) {
+    return C == 5 ? k_colx_fwd<Ar, 5, ZHALF, TFT> : C == 6 ? k_colx_fwd<Ar, 6, ZHALF, TFT>
+         : C == 7 ? k_colx_fwd<Ar, 7, ZHALF, TFT> : k_colx_fwd<Ar, 8, ZHALF, TFT>;
+}
+
+template <class Ar, bool TFT>
+auto colx_inv_kernel(int C) {
+    return C == 5 ? k_colx_inv<Ar, 5, TFT> : C == 6 ? k_colx_inv<Ar, 6, TFT>
+         : C == 7 ? k_colx_inv<Ar, 7, TFT> : k_colx_inv<Ar, 8, TFT>;
+}
+
 // The 2^16-point stage of a product of n = 2^17 .. 2^20 points: `count`
 // uniform sub-products at ws + s 2^17 (operand a) and + 2^16 (operand b),
 // transformed, multiplied and inverse-transformed in place by the child plan.
@@ -843,37 +855,63 @@ int launch_sub_products(const ntt_plan* core, typename Ar::word* ws, long long c
     return check_launch("sub-product passes");
 }
 
-// Products of n = 2^17 .. 2^20 points (Algorithm 1 with n1 = 2^16): the pass
+// Products of n = 2^17 .. 2^24 points (Algorithm 1 with n1 = 2^16): the pass
 // across the rows, the 2^16-point stage on the rows, the inverse pass.
-// Uniform batches keep only lam = ceil((na + nb - 1) / 2^16) rows (TFT);
-// uneven ones (desc) keep all n2.
+// Uniform batches keep only the rows their na + nb - 1 words need (TFT:
+// lam = ceil((na + nb - 1) / 2^16), rounded up to whole R2-row blocks for
+// n2 > 16); uneven ones (desc) keep all n2.
 template <class Ar>
 int launch_polymul_sub(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a, long long na,
                        const typename Ar::word* b, long long nb, long long batch, typename Ar::word* c,
                        typename Ar::word* ws, const BatchDesc* desc, cudaStream_t st) {
-    const int M = 1 << (static_cast<int>(plan->log2n) - kSubLog);
+    using word = typename Ar::word;
+    const int m = static_cast<int>(plan->log2n) - kSubLog;
+    const int M = 1 << m;
     const long long L = na + nb - 1;
-    const int lam = desc ? M : static_cast<int>(std::min<long long>(M, (L + kSubN - 1) / kSubN));
+    int lam = desc ? M : static_cast<int>(std::min<long long>(M, (L + kSubN - 1) / kSubN));
+    int B = 16;
+    if (M > 16) {                                       // column kernels: whole blocks of R2 rows
+        const int R2 = M / 16;
+        B = (lam + R2 - 1) / R2;
+        lam = B * R2;
+    }
     const bool tft = !desc && lam < M;
     const long long rows_stride = static_cast<long long>(lam) * 2 * kSubN;
     const auto* pre = static_cast<const typename Ar::tw*>(plan->pre_fwd);
     const auto* pre_inv = static_cast<const typename Ar::tw*>(plan->pre_inv);
+    const size_t smem_x = size_t(M) * kDCols * sizeof(word);
+    const bool zhalf = !desc && 2 * std::max(na, nb) <= (1LL << plan->log2n);
     prof_begin_call(st);
-    auto kpre = tft ? pre_kernel<Ar, true>(M) : pre_kernel<Ar, false>(M);
     for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
-        kpre<<<dim3(kSubN / kSubThreads, nbat, 2), kSubThreads, 0, st>>>(dp.ar, dp, a, na, na, b, nb, nb, ws,
-                                                                         rows_stride, 2 * kSubN, kSubN, pre, p0,
-                                                                         desc, lam);
+        if (M <= 16) {
+            auto kpre = tft ? pre_kernel<Ar, true>(M) : pre_kernel<Ar, false>(M);
+            kpre<<<dim3(kSubN / kSubThreads, nbat, 2), kSubThreads, 0, st>>>(dp.ar, dp, a, na, na, b, nb, nb, ws,
+                                                                             rows_stride, 2 * kSubN, kSubN, pre,
+                                                                             p0, desc, lam);
+        } else {
+            auto kx = tft ? (zhalf ? colx_fwd_kernel<Ar, true, true>(m) : colx_fwd_kernel<Ar, false, true>(m))
+                          : (zhalf ? colx_fwd_kernel<Ar, true, false>(m) : colx_fwd_kernel<Ar, false, false>(m));
+            if (allow_smem(kx, smem_x) != cudaSuccess) return check_launch("smem attr");
+            kx<<<dim3(kSubN / kDCols, nbat, 2), kDThreads, smem_x, st>>>(dp, a, na, na, b, nb, nb, ws, rows_stride,
+                                                                         2 * kSubN, kSubN, pre, p0, desc, B);
+        }
         prof_mark(st, "k_pre_fwd");
     }
     int rc = launch_sub_products<Ar>(plan->core, ws, batch * lam, st);
     if (rc != NTT_OK) return rc;
-    auto kpost = tft ? post_kernel<Ar, true>(M) : post_kernel<Ar, false>(M);
     for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
-        kpost<<<dim3(kSubN / kSubThreads, nbat, 1), kSubThreads, 0, st>>>(
-            dp.ar, dp, tft_consts<Ar>(plan), ws, rows_stride, 2 * kSubN, c, L, L, pre_inv, p0, desc, lam);
+        if (M <= 16) {
+            auto kpost = tft ? post_kernel<Ar, true>(M) : post_kernel<Ar, false>(M);
+            kpost<<<dim3(kSubN / kSubThreads, nbat, 1), kSubThreads, 0, st>>>(
+                dp.ar, dp, tft_consts<Ar>(plan), ws, rows_stride, 2 * kSubN, c, L, L, pre_inv, p0, desc, lam);
+        } else {
+            auto kx = tft ? colx_inv_kernel<Ar, true>(m) : colx_inv_kernel<Ar, false>(m);
+            if (allow_smem(kx, smem_x) != cudaSuccess) return check_launch("smem attr");
+            kx<<<dim3(kSubN / kDCols, nbat, 1), kDThreads, smem_x, st>>>(dp, tft_consts<Ar>(plan), ws, rows_stride,
+                                                                         2 * kSubN, c, L, L, pre_inv, p0, desc, B);
+        }
         prof_mark(st, "k_post_inv");
     }
     return check_launch("sub-vector passes");
@@ -915,15 +953,20 @@ int launch_ntt_direct(const DevPlan<Ar>& dp, typename Ar::word* data, long long 
     return check_launch("direct ntt passes");
 }
 
-// Standalone transforms of n = 2^17 .. 2^20 points in place (data 16-byte
+// Standalone transforms of n = 2^17 .. 2^24 points in place (data 16-byte
 // aligned): forward = pass across the rows, then 2^16-point transforms of the
 // rows by the child plan; inverse = the reverse.
 template <class Ar>
 int launch_ntt_sub(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* data, long long batch,
                    bool fwd, cudaStream_t st) {
-    const int M = 1 << (static_cast<int>(plan->log2n) - kSubLog);
+    using word = typename Ar::word;
+    const int m = static_cast<int>(plan->log2n) - kSubLog;
+    const int M = 1 << m;
     const long long n = static_cast<long long>(M) * kSubN;
     const DevPlan<Ar>& dpc = devplan_of<Ar>(plan->core);
+    const auto* pre = static_cast<const typename Ar::tw*>(plan->pre_fwd);
+    const auto* pre_inv = static_cast<const typename Ar::tw*>(plan->pre_inv);
+    const size_t smem_x = size_t(M) * kDCols * sizeof(word);
     int rc = NTT_OK;
     if (!fwd) {
         rc = launch_ntt_direct<Ar>(dpc, data, batch * M, false, st);
@@ -932,17 +975,24 @@ int launch_ntt_sub(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::wor
     prof_begin_call(st);
     for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
-        if (fwd) {
+        if (fwd && M <= 16) {
             pre_kernel<Ar, false>(M)<<<dim3(kSubN / kSubThreads, nbat, 1), kSubThreads, 0, st>>>(
-                dp.ar, dp, data, n, n, data, n, n, data, n, kSubN, 0,
-                static_cast<const typename Ar::tw*>(plan->pre_fwd), p0, nullptr, M);
-            prof_mark(st, "k_pre_fwd");
-        } else {
+                dp.ar, dp, data, n, n, data, n, n, data, n, kSubN, 0, pre, p0, nullptr, M);
+        } else if (fwd) {
+            auto kx = colx_fwd_kernel<Ar, false, false>(m);
+            if (allow_smem(kx, smem_x) != cudaSuccess) return check_launch("smem attr");
+            kx<<<dim3(kSubN / kDCols, nbat, 1), kDThreads, smem_x, st>>>(dp, data, n, n, data, n, n, data, n, kSubN,
+                                                                         0, pre, p0, nullptr, 16);
+        } else if (M <= 16) {
             post_kernel<Ar, false>(M)<<<dim3(kSubN / kSubThreads, nbat, 1), kSubThreads, 0, st>>>(
-                dp.ar, dp, TftConsts<Ar>{}, data, n, kSubN, data, n, n,
-                static_cast<const typename Ar::tw*>(plan->pre_inv), p0, nullptr, M);
-            prof_mark(st, "k_post_inv");
+                dp.ar, dp, TftConsts<Ar>{}, data, n, kSubN, data, n, n, pre_inv, p0, nullptr, M);
+        } else {
+            auto kx = colx_inv_kernel<Ar, false>(m);
+            if (allow_smem(kx, smem_x) != cudaSuccess) return check_launch("smem attr");
+            kx<<<dim3(kSubN / kDCols, nbat, 1), kDThreads, smem_x, st>>>(dp, TftConsts<Ar>{}, data, n, kSubN, data,
+                                                                         n, n, pre_inv, p0, nullptr, 16);
         }
+        prof_mark(st, fwd ? "k_pre_fwd" : "k_post_inv");
     }
     rc = check_launch("sub-vector pass");
     if (rc != NTT_OK || !fwd) return rc;

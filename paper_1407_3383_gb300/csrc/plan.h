@@ -34,10 +34,11 @@ struct ntt_plan {
     gbntt::Tw32 r32{};                          // 2^32 rem p (undoes a Montgomery product)
     gbntt::Tw64 r64{};                          // 2^64 rem p
     gbntt::TwF inv_scalef{};                    // n^-1 (FP64 plans; no Montgomery factor)
-    // n = 2^17 .. 2^20: Algorithm 1 with n1 = 2^16 and n2 = n / 2^16 -- a
-    // register pass across the n2 sub-vectors, then 2^16-point transforms by
-    // the child plan `core` (same modulus); pre_fwd[j2 2^16 + j1] =
-    // w_n^(j1 [j2]), pre_inv the inverse twiddles times n2^-1
+    // n = 2^17 .. 2^24: Algorithm 1 with n1 = 2^16 and n2 = n / 2^16 -- a
+    // pass across the n2 sub-vectors (in registers for n2 <= 16, a column
+    // kernel above), then 2^16-point transforms by the child plan `core`
+    // (same modulus); pre_fwd[j2 2^16 + j1] = w_n^(j1 [j2]), pre_inv the
+    // inverse twiddles times n2^-1
     ntt_plan* core = nullptr;
     const void* pre_fwd = nullptr;
     const void* pre_inv = nullptr;

@@ -388,7 +388,7 @@ static int finish_plan(ntt_plan* P, DevPlan<Ar>& dp, Conv conv, uint64_t pm_fact
     return NTT_OK;
 }
 
-// Tables of the pass across the n2 = n / 2^16 sub-vectors (n = 2^17 .. 2^20).
+// Tables of the pass across the n2 = n / 2^16 sub-vectors (n = 2^17 .. 2^24).
 template <class TwT, class Conv>
 static int build_pre_tables(ntt_plan* P, Conv conv) {
     const uint64_t p = P->p;
@@ -481,7 +481,7 @@ extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_p
         P->r64 = conv(r64);
         build_tft(P, P->tft64, conv);
     }
-    if (rc == NTT_OK && log2n >= 17 && log2n <= 20) {
+    if (rc == NTT_OK && log2n >= 17 && log2n <= 24) {
         rc = ntt_plan_create(p, 16, flags & ~NTT_FLAG_PLAIN, &P->core);
         if (rc == NTT_OK) {
             if (flags & NTT_FLAG_FP64)

@@ -45,7 +45,7 @@ LaunchCfg default_launch_cfg(unsigned word_bytes, int log2n, int tile_max_log) {
         c.lppc = (log2n <= kMaxLineLog) ? 4 : 0;
         return c;
     }
-    if (log2n >= 2 * kDLog && log2n <= 2 * kDLog + 4) return c;   // logw = 0: the direct kernels
+    if (log2n >= 2 * kDLog && log2n <= 3 * kDLog) return c;   // logw = 0: the direct kernels
     return generic_global_cfg(word_bytes, log2n);
 }
 
@@ -67,7 +67,7 @@ static bool cfg_valid(unsigned wb, int k, int tile_max_log, const LaunchCfg& c) 
     const size_t cap = 227 * 1024;
     if (k <= tile_max_log) return c.lppc >= 0 && c.lppc <= 6 && tile_smem_bytes(wb, k, c.lppc + 1) <= cap;
     const int k2 = k / 2, k1 = k - k2;
-    if (c.logw == 0) return k >= 2 * kDLog && k <= 2 * kDLog + 4;
+    if (c.logw == 0) return k >= 2 * kDLog && k <= 3 * kDLog;
     return c.logw >= 1 && c.logw <= k1 && col_smem_bytes(wb, k2, c.logw) <= cap && c.lrpc >= 0 &&
            c.lrpc <= k2 && tile_smem_bytes(wb, k1, c.lrpc + 1) <= cap;
 }

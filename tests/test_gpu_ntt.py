@@ -65,6 +65,7 @@ def _check_sampled(p, log2n, a, fwd, batch, samples=48, seed=1):
     (W.P1, 14, 2), (W.P2, 17, 1), (W.P1, 20, 1),          # two global passes (u64)
     (W.P3, 16, 3),                                        # direct 256 x 256 kernels (u64)
     (W.P_B, 17, 2), (W.P_A, 19, 1), (W.P3, 18, 2),        # pass across 2^16-point rows + direct kernels
+    (W.P_B, 21, 1), (W.P2, 22, 1), (W.P_A, 23, 1),        # column kernel across 32..128 rows
 ])
 def test_forward_sampled_and_roundtrip(p, log2n, batch):
     n = 1 << log2n

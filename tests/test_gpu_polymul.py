@@ -217,12 +217,15 @@ def _generic_vs_default(p, log2n, a, b):
     (W.P_B, 17, 65537), (W.P_B, 17, 131071),                        # n2 = 2: one row (TFT), both rows
     (W.P1, 18, 65536), (W.P1, 18, 131073), (W.P1, 18, 196608), (W.P1, 18, 262143),   # every row count
     (W.P_A, 19, 300001), (W.P2, 20, 70000), (W.P3, 20, 1048575),
+    (W.P_B, 21, (1 << 20) + 5), (W.P_B, 21, 2097151),               # n2 = 32: 1 of 16 blocks (TFT), all
+    (W.P1, 22, 3 << 20), (W.P_A, 23, (5 << 20) + 3), (W.P3, 24, 16777215), (W.P2, 24, 9 << 20),
 ])
-def test_products_2e17_to_2e20(p, log2n, L):
-    """n = 2^17 .. 2^20: Algorithm 1 with 2^16-point rows (a pass across the
-    rows, the direct kernels on the rows, the inverse pass), truncated to the
-    rows the output needs; equal to the padded generic passes and the oracle
-    on sampled coefficients and fingerprints."""
+def test_products_2e17_to_2e24(p, log2n, L):
+    """n = 2^17 .. 2^24: Algorithm 1 with 2^16-point rows (a pass across the
+    rows -- in registers up to 16 rows, a column kernel above -- the direct
+    kernels on the rows, the inverse pass), truncated to the rows the output
+    needs; equal to the padded generic passes and the oracle on sampled
+    coefficients and fingerprints."""
     g = W.SplitMix64(L + log2n)
     na = (L + 1) // 2 + 17
     nb = L + 1 - na

@@ -27,8 +27,8 @@ def test_default_shapes():
     # one-block sizes: 16 products per block for short vectors, 1 for tiles
     assert G.ntt_tune_get(4, 8)[0] == 4
     assert G.ntt_tune_get(8, 12)[0] == 0
-    # n = 2^16 .. 2^20 above the one-block limit: the direct kernels (logw = 0)
-    for k in range(16, 21):
+    # n = 2^16 .. 2^24 above the one-block limit: the direct kernels (logw = 0)
+    for k in range(16, 25):
         assert G.ntt_tune_get(4, k)[1] == 0 and G.ntt_tune_get(8, k)[1] == 0
-    assert G.ntt_tune_get(4, 21)[1] >= 1 and G.ntt_tune_get(4, 15)[1] >= 1
+    assert G.ntt_tune_get(4, 15)[1] >= 1
 
