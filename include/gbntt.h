@@ -115,9 +115,13 @@ int ntt_fixed_companion(uint64_t p, unsigned kind, unsigned word_bytes, const ui
  * current CUDA device: checks p (prime, odd, < 2^62, 16 | p-1) and
  * 2^log2n | p-1, builds the root-of-unity tables on the host (Section 5.1:
  * all powers precomputed and cached) and copies them to the device once.
- * 1 <= log2n <= 24.  flags: NTT_FLAG_*.  The plan owns its device tables;
- * free it with ntt_plan_destroy.  Errors: NTT_ERR_ARG, NTT_ERR_MODULUS,
- * NTT_ERR_NOT_PRIME, NTT_ERR_NO_ROOT, NTT_ERR_SIZE, NTT_ERR_OOM, NTT_ERR_CUDA. */
+ * For log2n = 17 .. 24 the plan also owns a 2^16-point plan of the same
+ * modulus and a table of 2n twiddles (the transform is Algorithm 1 over
+ * 2^16-point rows).  1 <= log2n <= 24.  flags: NTT_FLAG_*.  The plan owns
+ * its device tables; free it with ntt_plan_destroy.  Errors: NTT_ERR_ARG,
+ * NTT_ERR_MODULUS, NTT_ERR_NOT_PRIME, NTT_ERR_NO_ROOT, NTT_ERR_SIZE,
+ * NTT_ERR_OOM, NTT_ERR_CUDA, NTT_ERR_UNSUPPORTED (NTT_FLAG_FP64 with
+ * NTT_FLAG_PLAIN). */
 int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_plan** out);
 
 /* Free the plan and its device tables (synchronises the plan's device). */
@@ -131,7 +135,9 @@ int ntt_plan_get_info(const ntt_plan* plan, ntt_plan_info* out);
 /* In-place forward transform of `batch` vectors of n words stored back to
  * back at d_data: vector v becomes TFT_omega with l = n (Section 5.1),
  * i.e. word i holds A(omega^[i]) where [i] mirrors the log2n bits of i.
- * Inputs must be residues < p. */
+ * Inputs must be residues < p (NTT_FLAG_FP64 plans: doubles holding them).
+ * For n = 2^16 .. 2^24 the fast passes need d_data 16-byte aligned; data
+ * that is only word-aligned gets the same result from slower passes. */
 int ntt_forward(const ntt_plan* plan, void* d_data, size_t batch, void* stream);
 
 /* In-place inverse: consumes the bit-mirrored order ntt_forward produces and
@@ -150,7 +156,9 @@ size_t polymul_workspace_size(const ntt_plan* plan, size_t batch, unsigned sched
  * back to back.  Requires 1 <= na, nb and na + nb - 1 <= n: the product is
  * the size-n cyclic convolution of the zero-padded operands, which equals the
  * linear product when no coefficient wraps.  Two forward transforms, the
- * pointwise product and one inverse transform (Section 5.2).  schedule:
+ * pointwise product and one inverse transform (Section 5.2); for n = 2^16 ..
+ * 2^24 the transforms are truncated (TFT, Section 5.1) to the rows that the
+ * na + nb - 1 output words need, which changes nothing in c.  schedule:
  * NTT_SCHED_FUSED or NTT_SCHED_PLAIN (the latter needs NTT_FLAG_PLAIN).
  * d_ws: at least polymul_workspace_size bytes, 256-byte aligned (may be
  * NULL when that size is 0). */
