@@ -100,6 +100,7 @@ def fused_kernel_ops(log2n: int, na: int, nb: int, batch: int, tile_max_log: int
     ops = {"k_col_fwd": col_fwd * batch, "k_row_polymul": row * batch, "k_col_inv": col_inv * batch}
     # the direct 2^16-point kernels do the same work in the same three launches
     ops.update({name + "_d": v for name, v in ops.items()})
+    ops["k_col_fwd_tma"] = ops["k_col_fwd"]            # the same pass with its input tile by TMA
     return ops
 
 
@@ -366,8 +367,11 @@ def run_native(args, world, rank, local):
     tuned_ms = None if args.no_autotune else G.ntt_autotune(plan, batch, stream=stream)
     shape = dict(zip(["log2_products_per_block", "log2_columns_per_block", "log2_rows_per_block"],
                      G.ntt_tune_get(plan.word_bytes, log2n)))
-    shape["kernels"] = ("direct 256 x 256" if log2n == 16 and shape["log2_columns_per_block"] == 0
-                        else "generic")
+    direct = log2n >= 16 and shape["log2_columns_per_block"] == 0
+    shape["kernels"] = ("direct 256 x 256" + (", operand tiles by TMA" if shape["log2_products_per_block"] & 1
+                                              else "") if direct else "generic")
+    if direct:
+        del shape["log2_products_per_block"], shape["log2_columns_per_block"], shape["log2_rows_per_block"]
 
     def flush():
         flush_buf.fill_(1)

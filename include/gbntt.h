@@ -307,9 +307,10 @@ int ntt_server_destroy(ntt_server* server);
  * best time in ms to *best_ms when non-null.  Synchronous. */
 int ntt_autotune(const ntt_plan* plan, size_t batch, void* stream, float* best_ms);
 /* The shape currently used for (word_bytes, log2n): products per block,
- * columns per block and rows per block, each as log2.  For n = 2^16 above
- * the one-block limit, logw = 0 (the default) selects the direct
- * 256 x 256 kernels, whose block shape is fixed (lrpc is then ignored). */
+ * columns per block and rows per block, each as log2.  For n = 2^16 .. 2^24
+ * above the one-block limit, logw = 0 (the default) selects the direct
+ * kernels, whose block shape is fixed (lrpc is then ignored); at n = 2^16,
+ * lppc = 1 makes them bring zero-half operand tiles in by TMA. */
 int ntt_tune_get(unsigned word_bytes, unsigned log2n, int* lppc, int* logw, int* lrpc);
 /* Forget every tuned or imported shape (back to the defaults). */
 int ntt_tune_reset(void);
@@ -383,6 +384,12 @@ int ntt_modmul_vec(uint64_t p, unsigned kind, unsigned word_bytes, const uint64_
 int ntt_modmul_rate(uint64_t p, unsigned kind, unsigned word_bytes, int iters, double* products_per_s);
 
 /* ---- diagnostics --------------------------------------------------------- */
+
+/* NTT_OK, or NTT_ERR_TIMEOUT when a kernel's bounded wait for a tensor-
+ * memory-accelerator (TMA) copy on the current device ran out since the
+ * last call (the kernel then returned without writing its results; the flag
+ * is cleared by this call).  Synchronous (reads one device word). */
+int ntt_device_status(void);
 
 /* Launch profiling (the paper has no counterpart; it reports CPU user time
  * per transform, Section 5.1).  After ntt_profile_begin(), every library

@@ -113,6 +113,7 @@ def _load():
             "ntt_tune_export": (_int, [ctypes.c_char_p, _sz, ctypes.POINTER(_sz)]),
             "ntt_tune_import": (_int, [ctypes.c_char_p]),
             "ntt_tune_reset": (_int, []),
+            "ntt_device_status": (_int, []),
             "ntt_server_create": (_int, [_vp, ctypes.POINTER(_vp)]),
             "ntt_server_submit": (_int, [_vp, _uint, _uint, _vp, _sz, _vp, _sz, _vp, _uint,
                                          ctypes.POINTER(_u64)]),
@@ -449,6 +450,11 @@ def ntt_tune_export() -> str:
 
 def ntt_tune_import(text: str):
     _check(_load().ntt_tune_import(text.encode()), "ntt_tune_import")
+
+
+def ntt_device_status():
+    """Raise NttError(NTT_ERR_TIMEOUT) if a kernel's bounded TMA wait ran out."""
+    _check(_load().ntt_device_status(), "ntt_device_status")
 
 
 def ntt_tune_reset():

@@ -25,6 +25,7 @@
 
 #include "engine.cuh"
 #include "tft.cuh"
+#include "tma.cuh"
 
 namespace gbntt {
 
@@ -117,6 +118,69 @@ k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long
             tdif16<Ar, ZHALF>(P.ar, x, P.rc, B);
         else
             dif_regs<Ar, 16, ZHALF>(P.ar, x, P.rc);
+#pragma unroll
+        for (int t = 1; t < 16; ++t)
+            if (!TFT || t < B) x[t] = P.ar.mulw(x[t], ltab[j1 * 16 + t]);
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+            if (!TFT || t < B) sm[(16 * t + j1) * kDCols + v] = x[t];
+    }
+    __syncthreads();
+    word* out = dst + prod * dst_stride + (blockIdx.z ? dst_off1 : 0) + c0 + v;
+    const tw* gt = P.glob_fwd + c0 + v;
+#pragma unroll
+    for (int i = 0; i < kDItems; ++i) {
+        const int blk = g + kDGroups * i;
+        if (TFT && blk >= B) continue;
+        word x[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) x[t] = sm[(16 * blk + t) * kDCols + v];
+        dif_regs<Ar, 16>(P.ar, x, P.rc);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const long long pos = 16 * blk + t;
+            out[pos * kDLine] = P.ar.mulw(x[t], gt[pos * kDLine]);
+        }
+    }
+}
+
+// k_col_fwd_d for uniform batches of zero-half operands made of whole
+// 256-word rows, with the input tile brought in by one TMA copy: operand z of
+// product prod is the 3-D tensor (256 columns, na/256 rows, batch) of
+// map_a / map_b, and the box (32 columns, 128 rows) at (c0, 0, prod) -- rows
+// past the operand are the copy's zero fill -- lands in shared memory in the
+// layout the outer pass reads (row r, column v at r*32 + v).  Each thread
+// then reads its 8 rows 16 t + j1 and writes its 16 outputs to the same
+// positions, which no other thread touches.
+template <class Ar, bool TFT>
+__global__ void __launch_bounds__(kDThreads)
+k_col_fwd_tma(DevPlan<Ar> P, const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+              typename Ar::word* __restrict__ dst, long long dst_stride, long long dst_off1, long long prod_base,
+              int beta, int* err) {
+    using word = typename Ar::word;
+    using tw = typename Ar::tw;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    word* sm = reinterpret_cast<word*>(smraw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smraw + direct_col_smem_words() * sizeof(word));
+    const int v = threadIdx.x & (kDCols - 1), g = threadIdx.x / kDCols;
+    const long long c0 = static_cast<long long>(blockIdx.x) * kDCols;
+    const long long prod = prod_base + blockIdx.y;
+    const CUtensorMap* map = blockIdx.z ? &map_b : &map_a;
+    if (!tma_block_load_3d(sm, map, static_cast<int>(c0), 0, static_cast<int>(prod),
+                           static_cast<unsigned>(kDCols * (kDLine / 2) * sizeof(word)), bar, err))
+        return;
+    const int B = TFT ? beta : 16;
+    const tw* ltab = P.line_fwd[kDLog];
+#pragma unroll
+    for (int i = 0; i < kDItems; ++i) {
+        const int j1 = g + kDGroups * i;
+        word x[16];
+#pragma unroll
+        for (int t = 0; t < 16; ++t) x[t] = (t < 8) ? sm[(16 * t + j1) * kDCols + v] : word(0);
+        if (TFT)
+            tdif16<Ar, true>(P.ar, x, P.rc, B);
+        else
+            dif_regs<Ar, 16, true>(P.ar, x, P.rc);
 #pragma unroll
         for (int t = 1; t < 16; ++t)
             if (!TFT || t < B) x[t] = P.ar.mulw(x[t], ltab[j1 * 16 + t]);

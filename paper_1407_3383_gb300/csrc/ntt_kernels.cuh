@@ -759,7 +759,7 @@ template <class Ar>
 int launch_polymul_direct(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
                           long long na, const typename Ar::word* b, long long nb, long long batch,
                           typename Ar::word* c, typename Ar::word* ws, const BatchDesc* desc,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool want_tma = false) {
     using word = typename Ar::word;
     constexpr long long N = 1LL << (2 * kDLog);
     const size_t smem_c = direct_col_smem_words() * sizeof(word);
@@ -778,11 +778,36 @@ int launch_polymul_direct(const ntt_plan* plan, const DevPlan<Ar>& dp, const typ
         return check_launch("smem attr");
     const auto* itab = static_cast<const typename Ar::tw*>(plan->glob_inv_pm);
     const unsigned row_blocks = static_cast<unsigned>(16 * (tft ? beta : 16) / kDRowsPerBlock);
+    // TMA tiles (shape-table choice) for zero-half operands of whole rows
+    // (16-byte aligned bases)
+    CUtensorMap map_a{}, map_b{};
+    bool tma = want_tma && zhalf && na % kDLine == 0 && nb % kDLine == 0 && batch < (1LL << 31);
+    if (tma) {
+        const CUtensorMapDataType dt = sizeof(word) == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32
+                                       : std::is_same<word, double>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                                                            : CU_TENSOR_MAP_DATA_TYPE_UINT64;
+        const uint32_t box[3] = {kDCols, kDLine / 2, 1};
+        const uint64_t da[3] = {kDLine, static_cast<uint64_t>(na / kDLine), static_cast<uint64_t>(batch)};
+        const uint64_t db[3] = {kDLine, static_cast<uint64_t>(nb / kDLine), static_cast<uint64_t>(batch)};
+        const uint64_t sa[2] = {kDLine * sizeof(word), static_cast<uint64_t>(na) * sizeof(word)};
+        const uint64_t sb[2] = {kDLine * sizeof(word), static_cast<uint64_t>(nb) * sizeof(word)};
+        tma = encode_tensor_map_3d(&map_a, dt, const_cast<word*>(a), da, sa, box) &&
+              encode_tensor_map_3d(&map_b, dt, const_cast<word*>(b), db, sb, box);
+    }
+    int* err = tma ? device_error_flag() : nullptr;
+    tma = tma && err;
+    auto kct = tft ? k_col_fwd_tma<Ar, true> : k_col_fwd_tma<Ar, false>;
+    const size_t smem_t = smem_c + 16;
+    if (tma && allow_smem(kct, smem_t) != cudaSuccess) return check_launch("smem attr");
     for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
-        kcf<<<dim3(kDLine / kDCols, nbat, 2), kDThreads, smem_c, st>>>(dp, a, na, na, b, nb, nb, ws, 2 * N, N, p0,
-                                                                       desc, tft ? beta : 16);
-        prof_mark(st, tft ? "k_col_fwd_d_tft" : "k_col_fwd_d");
+        if (tma)
+            kct<<<dim3(kDLine / kDCols, nbat, 2), kDThreads, smem_t, st>>>(dp, map_a, map_b, ws, 2 * N, N, p0,
+                                                                           tft ? beta : 16, err);
+        else
+            kcf<<<dim3(kDLine / kDCols, nbat, 2), kDThreads, smem_c, st>>>(dp, a, na, na, b, nb, nb, ws, 2 * N, N,
+                                                                           p0, desc, tft ? beta : 16);
+        prof_mark(st, tma ? (tft ? "k_col_fwd_tma_tft" : "k_col_fwd_tma") : (tft ? "k_col_fwd_d_tft" : "k_col_fwd_d"));
         krp<<<dim3(row_blocks, nbat, 1), kDRowsPerBlock * 16, smem_r, st>>>(dp, ws, 2 * N, p0, desc);
         prof_mark(st, tft ? "k_row_polymul_d_tft" : "k_row_polymul_d");
         kci<<<dim3(kDLine / kDCols, nbat, 1), kDThreads, smem_c, st>>>(dp, ws, 2 * N, c, na + nb - 1,
@@ -1023,7 +1048,8 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
         }
         return check_launch("k_tile_polymul");
     }
-    if (cfg.logw == 0 && k == 2 * kDLog) return launch_polymul_direct<Ar>(plan, dp, a, na, b, nb, batch, c, ws, nullptr, st);
+    if (cfg.logw == 0 && k == 2 * kDLog)
+        return launch_polymul_direct<Ar>(plan, dp, a, na, b, nb, batch, c, ws, nullptr, st, (cfg.lppc & 1) != 0);
     if (cfg.logw == 0 && plan->core) return launch_polymul_sub<Ar>(plan, dp, a, na, b, nb, batch, c, ws, nullptr, st);
     const int k2 = plan->k2, k1 = plan->k1;
     const long long N = 1LL << k;

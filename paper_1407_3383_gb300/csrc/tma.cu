@@ -1,0 +1,78 @@
+// Host side of the TMA loads and the device error flag.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "../../include/gbntt.h"
+#include "plan.h"
+#include "tma.cuh"
+
+namespace gbntt {
+
+__device__ int g_device_error = 0;
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+}  // namespace
+
+bool encode_tensor_map_3d(CUtensorMap* map, CUtensorMapDataType type, void* base, const uint64_t dims[3],
+                          const uint64_t strides_bytes[2], const uint32_t box[3]) {
+    EncodeTiledFn fn = encoder();
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+    const cuuint64_t gdim[3] = {dims[0], dims[1], dims[2]};
+    const cuuint64_t gstr[2] = {strides_bytes[0], strides_bytes[1]};
+    const cuuint32_t bdim[3] = {box[0], box[1], box[2]};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, type, 3, base, gdim, gstr, bdim, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int* device_error_flag() {
+    static std::mutex mu;
+    static int* by_device[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!by_device[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        by_device[dev] = static_cast<int*>(p);
+    }
+    return by_device[dev];
+}
+
+}  // namespace gbntt
+
+using namespace gbntt;
+
+extern "C" int ntt_device_status(void) {
+    int flag = 0;
+    if (cudaMemcpyFromSymbol(&flag, g_device_error, sizeof(int)) != cudaSuccess) return NTT_ERR_CUDA;
+    if (!flag) return NTT_OK;
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int));
+    gbntt_set_error("a kernel's bounded wait for a tensor-memory-accelerator copy ran out");
+    return NTT_ERR_TIMEOUT;
+}

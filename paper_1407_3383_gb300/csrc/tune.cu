@@ -191,6 +191,11 @@ extern "C" int ntt_autotune(const ntt_plan* plan, size_t batch, void* stream, fl
             if (t < g_t) g_t = t, g = cfg;
         }
         if (g_t < best_t) best_t = g_t, best = g;
+        if (k == 2 * kDLog) {                          // direct kernels with TMA input tiles
+            LaunchCfg t{1, 0, 0};
+            const float tt = try_cfg(t);
+            if (tt < best_t) best_t = tt, best = t;
+        }
     }
     set_launch_cfg(wb, k, best);
     if (best_ms) *best_ms = best_t;

@@ -100,10 +100,18 @@ def _sampled_check(p, a, b, got, samples, seed):
 @pytest.mark.parametrize("schedule", [G.NTT_SCHED_FUSED, G.NTT_SCHED_PLAIN])
 def test_config1_full_size_sampled(schedule):
     """256 products mod 3*2^30+1 of length-2^15 operands (size-2^16
-    transforms), exactly as the benchmark runs them."""
+    transforms), exactly as the benchmark runs them (fused: also with the
+    operand tiles brought in by TMA, the device error flag staying clear)."""
     p, a, b = W.config1()
     flags = G.NTT_FLAG_PLAIN if schedule == G.NTT_SCHED_PLAIN else 0
     got = _polymul(p, 16, a, b, schedule, flags)
+    if schedule == G.NTT_SCHED_FUSED:                  # the same product with TMA operand tiles
+        try:
+            G.ntt_tune_import("4 16 1 0 0\n")
+            assert (_polymul(p, 16, a, b, schedule, flags) == got).all()
+            G.ntt_device_status()
+        finally:
+            G.ntt_tune_reset()
     _sampled_check(p, a.astype(np.uint64), b.astype(np.uint64), got, 64, 11)
     # a few products in full against the schoolbook oracle
     idx = [0, 255]
@@ -234,4 +242,25 @@ def test_products_2e17_to_2e24(p, log2n, L):
     got, padded = _generic_vs_default(p, log2n, a, b)
     assert (got == padded).all()
     _sampled_check(p, a, b, got, 32, L)
+
+
+@pytest.mark.parametrize("p,na,nb", [(W.P_B, 256 * 100, 256 * 37), (W.P1, 256 * 128, 256), (W.P_A, 256, 256)])
+def test_tma_tiles_partial_rows(p, na, nb):
+    """With the TMA shape (lppc = 1), whole-row operands shorter than n/2
+    take the TMA column kernel, whose copy zero-fills the rows past each
+    operand; compare with the oracle and the plain-load kernels."""
+    g = W.SplitMix64(na + 3 * nb)
+    a = g.uniform_mod(p, 2 * na).reshape(2, na)
+    b = g.uniform_mod(p, 2 * nb).reshape(2, nb)
+    wb = 4 if p < (1 << 32) else 8
+    G.ntt_tune_reset()
+    plain = _polymul(p, 16, a, b)
+    try:
+        G.ntt_tune_import(f"{wb} 16 1 0 0\n")
+        got = _polymul(p, 16, a, b)
+        G.ntt_device_status()
+    finally:
+        G.ntt_tune_reset()
+    assert (got == plain).all()
+    assert (got == O.polymul_batch(p, a, b)).all()
 
