@@ -158,10 +158,15 @@ __device__ __forceinline__ uint64_t slice64(const uint64_t* w, long long off) {
 // Word j of sum_k c_k 2^(h k) before carries: the 64-bit slices of the
 // coefficients overlapping bits [64 j, 64 j + 64), as (low word, high part
 // <= 3).  With h = 64 these are w0(c_j) + w1(c_{j-1}) + w2(c_{j-2}).
+template <bool H64>
 __device__ __forceinline__ void column_sum(const uint64_t* W, long long nc, long long j, int h, uint64_t& lo,
                                            uint64_t& hi) {
     u128 s = 0;
-    if (j >= 0) {
+    if (H64) {                                      // word-aligned coefficients: three fixed terms
+        if (j >= 0 && j < nc) s += W[3 * j];
+        if (j - 1 >= 0 && j - 1 < nc) s += W[3 * (j - 1) + 1];
+        if (j - 2 >= 0 && j - 2 < nc) s += W[3 * (j - 2) + 2];
+    } else if (j >= 0) {
         const long long top = 64 * j + 63;
         long long k = (64 * j - 191 + h - 1) / h;   // first k with h k + 192 > 64 j
         if (64 * j - 191 <= 0) k = 0;
@@ -173,10 +178,11 @@ __device__ __forceinline__ void column_sum(const uint64_t* W, long long nc, long
 }
 
 // u_j = lo_j + hi_{j-1}: its low word v_j and its carry state.
+template <bool H64>
 __device__ __forceinline__ uint8_t word_state(const uint64_t* W, long long nc, long long j, int h, uint64_t& v) {
     uint64_t lo, hi, plo, phi;
-    column_sum(W, nc, j, h, lo, hi);
-    column_sum(W, nc, j - 1, h, plo, phi);
+    column_sum<H64>(W, nc, j, h, lo, hi);
+    column_sum<H64>(W, nc, j - 1, h, plo, phi);
     const u128 u = static_cast<u128>(lo) + phi;
     v = static_cast<uint64_t>(u);
     if (u >> 64) return kGen;
@@ -191,6 +197,7 @@ __device__ __forceinline__ void store_word(uint32_t* c, long long nlimbs, long l
 // Pass 1: per word its carry-free value (stored into c) and its carry state
 // relative to the start of its block (stored into st); per block the state
 // of the whole block (agg).
+template <bool H64>
 __global__ void __launch_bounds__(kCarryThreads)
 k_carry_local(const uint64_t* __restrict__ W, long long nc, long long nwords, int h, uint32_t* __restrict__ c,
               long long nlimbs, uint8_t* __restrict__ st, uint8_t* __restrict__ agg, long long nblocks) {
@@ -208,7 +215,7 @@ k_carry_local(const uint64_t* __restrict__ W, long long nc, long long nwords, in
         uint64_t v = 0;
         s[e] = kKill;
         if (j < nwords) {
-            s[e] = word_state(W, nc, j, h, v);
+            s[e] = word_state<H64>(W, nc, j, h, v);
             store_word(c, nlimbs, j, v);
         }
         tot = carry_combine(tot, s[e]);
@@ -493,7 +500,7 @@ extern "C" int intmul_crt(const intmul_plan* plan, const uint32_t* d_a, size_t n
     if (rc != NTT_OK) return rc;
     k_crt<<<grid_of(L.nc, 256), 256, 0, st>>>(res, L.nc, L.nc, W, C);
     prof_mark(st, "k_crt");
-    k_carry_local<<<static_cast<unsigned>(L.nblocks), kCarryThreads, 0, st>>>(
+    (L.h == 64 ? k_carry_local<true> : k_carry_local<false>)<<<static_cast<unsigned>(L.nblocks), kCarryThreads, 0, st>>>(
         W, L.nc, L.nwords, L.h, d_c, static_cast<long long>(na + nb), sst, agg, L.nblocks);
     prof_mark(st, "k_carry_local");
     k_carry_blocks<<<1, 1024, 0, st>>>(agg, L.nblocks);
@@ -598,7 +605,7 @@ extern "C" int intmat_mul(const intmul_plan* plan, const uint32_t* d_A, size_t n
     k_crt<<<grid_of(L.nn * L.nc, 256), 256, 0, st>>>(res, L.nn * L.nc, L.nn * L.nc, W, C);
     prof_mark(st, "k_crt");
     const unsigned ny = static_cast<unsigned>(L.nn);
-    k_carry_local<<<dim3(static_cast<unsigned>(L.nblocks), ny), kCarryThreads, 0, st>>>(
+    k_carry_local<true><<<dim3(static_cast<unsigned>(L.nblocks), ny), kCarryThreads, 0, st>>>(
         W, L.nc, L.nwords, 64, d_C, nlimbs, sst, agg, L.nblocks);
     prof_mark(st, "k_carry_local");
     k_carry_blocks<<<ny, 1024, 0, st>>>(agg, L.nblocks);

@@ -622,6 +622,98 @@ k_polymat_freq_s(Mont32 ar, const uint32_t* __restrict__ At, const uint32_t* __r
     }
 }
 
+// The same for 64-bit words (Shoup64L, p < 2^62): 128-bit sums of the
+// products, folded every K = floor((2^64 - 1) / (p - 1)) terms (so a sum is
+// below p 2^64) by one Montgomery reduction to s 2^-64 rem p; the final
+// product by r = 2^64 rem p removes the 2^-64.  4 frequencies per block at
+// n = 32 to fit shared memory.
+template <int NN>
+struct PmShared64 {
+    static constexpr int NT = NN / 4, TPF = NT * NT;
+    static constexpr int F = (256 / TPF) > 4 ? (256 / TPF) : 4;
+    static constexpr int THREADS = F * TPF;
+    static constexpr int AS = NN + 1;
+    static constexpr int AF = NN * AS + 1 + ((NN * AS + 1) & 1);   // even: keeps B 16-byte aligned
+    static constexpr int BF = NN * NN + 2;
+    static constexpr size_t words = size_t(F) * (AF + BF);
+};
+
+template <int NN>
+__global__ void __launch_bounds__(PmShared64<NN>::THREADS)
+k_polymat_freq_s64(Shoup64L ar, const uint64_t* __restrict__ At, const uint64_t* __restrict__ Bt,
+                   uint64_t* __restrict__ Ct, int logN, Tw64 r, int K) {
+    using S = PmShared64<NN>;
+    using u128 = unsigned __int128;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    uint64_t* sA = reinterpret_cast<uint64_t*>(smraw);
+    uint64_t* sB = sA + S::F * S::AF;
+    const long long N = 1LL << logN;
+    const long long k0 = static_cast<long long>(blockIdx.x) * S::F;
+    const int tid = threadIdx.x;
+#pragma unroll 4
+    for (int it = 0; it < NN * NN * S::F / S::THREADS; ++it) {
+        const int idx = it * S::THREADS + tid;
+        const int f = idx % S::F, e = idx / S::F;
+        const bool in = k0 + f < N;
+        const long long g = (static_cast<long long>(e) << logN) + k0 + f;
+        sA[f * S::AF + (e / NN) * S::AS + (e % NN)] = in ? At[g] : 0ull;
+        sB[f * S::BF + e] = in ? Bt[g] : 0ull;
+    }
+    __syncthreads();
+    const int f = tid / S::TPF, tile = tid % S::TPF;
+    const int i0 = (tile / S::NT) * 4, j0 = (tile % S::NT) * 4;
+    const uint64_t* a_f = sA + f * S::AF + i0 * S::AS;
+    const uint64_t* b_f = sB + f * S::BF + j0;
+    uint64_t res[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) res[u][v] = 0;
+    for (int l0 = 0; l0 < NN; l0 += K) {
+        u128 acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+        const int l1 = min(NN, l0 + K);
+        for (int l = l0; l < l1; ++l) {
+            uint64_t a[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = a_f[u * S::AS + l];
+            const ulonglong2 b01 = *reinterpret_cast<const ulonglong2*>(b_f + l * NN);
+            const ulonglong2 b23 = *reinterpret_cast<const ulonglong2*>(b_f + l * NN + 2);
+            const uint64_t b[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += static_cast<u128>(a[u]) * b[v];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const uint64_t lo = static_cast<uint64_t>(acc[u][v]), hi = static_cast<uint64_t>(acc[u][v] >> 64);
+                const uint64_t q = lo * ar.pinv;
+                const uint64_t t = __umul64hi(q, ar.p);
+                const uint64_t red = (hi >= t) ? hi - t : hi - t + ar.p;
+                res[u][v] = ar.add(res[u][v], red);
+            }
+    }
+    __syncthreads();
+    uint64_t* c_f = sB + f * S::BF + i0 * NN + j0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) c_f[u * NN + v] = ar.canon(ar.mulw(res[u][v], r));
+    __syncthreads();
+#pragma unroll 4
+    for (int it = 0; it < NN * NN * S::F / S::THREADS; ++it) {
+        const int idx = it * S::THREADS + tid;
+        const int ff = idx % S::F, e = idx / S::F;
+        if (k0 + ff < N) Ct[(static_cast<long long>(e) << logN) + k0 + ff] = sB[ff * S::BF + e];
+    }
+}
+
 template <class Ar>
 __global__ void k_polymat_crop(Ar ar, const typename Ar::word* __restrict__ ws, typename Ar::word* __restrict__ C,
                                long long nn, long long dc, int logN) {
@@ -1177,6 +1269,19 @@ int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* d
                bool fwd, typename Ar::tw scale, cudaStream_t st);
 
 template <int NN>
+int launch_polymat_freq_s64(const Shoup64L& ar, const uint64_t* At, const uint64_t* Bt, uint64_t* Ct, int logN,
+                            Tw64 r, cudaStream_t st) {
+    using S = PmShared64<NN>;
+    const size_t smem = S::words * sizeof(uint64_t);
+    if (allow_smem(k_polymat_freq_s64<NN>, smem) != cudaSuccess) return check_launch("smem attr");
+    const long long N = 1LL << logN;
+    const int K = static_cast<int>(std::min<uint64_t>(~uint64_t(0) / (ar.p - 1), 1u << 30));
+    k_polymat_freq_s64<NN><<<static_cast<unsigned>((N + S::F - 1) / S::F), S::THREADS, smem, st>>>(
+        ar, At, Bt, Ct, logN, r, K);
+    return NTT_OK;
+}
+
+template <int NN>
 int launch_polymat_freq_s(const Mont32& ar, const uint32_t* At, const uint32_t* Bt, uint32_t* Ct, int logN,
                           Tw32 r, int K, cudaStream_t st) {
     using S = PmShared<NN>;
@@ -1251,6 +1356,14 @@ int launch_polymat(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename A
                 const int rc = n == 8    ? launch_polymat_freq_s<8>(dp.ar, At, Bt, Ct, k, r, K, st)
                                : n == 16 ? launch_polymat_freq_s<16>(dp.ar, At, Bt, Ct, k, r, K, st)
                                          : launch_polymat_freq_s<32>(dp.ar, At, Bt, Ct, k, r, K, st);
+                if (rc != NTT_OK) return rc;
+                done = true;
+            }
+        } else if constexpr (std::is_same<Ar, Shoup64L>::value) {
+            if (n == 8 || n == 16 || n == 32) {
+                const int rc = n == 8    ? launch_polymat_freq_s64<8>(dp.ar, At, Bt, Ct, k, r, st)
+                               : n == 16 ? launch_polymat_freq_s64<16>(dp.ar, At, Bt, Ct, k, r, st)
+                                         : launch_polymat_freq_s64<32>(dp.ar, At, Bt, Ct, k, r, st);
                 if (rc != NTT_OK) return rc;
                 done = true;
             }

@@ -33,6 +33,7 @@ def _polymat(p, log2n, A, B):
     (W.P_TABLE11, 32, 100, 8),     # shared-memory frequency kernel, one fold per output
     (W.P_A, 32, 33, 7),            # 32 x 32 over 998244353 (several terms per fold)
     (W.P_TABLE11, 8, 5, 4),        # fewer frequencies than a block holds
+    (W.P1, 8, 50, 7), (W.P3, 16, 20, 6), (W.P2, 32, 9, 5),   # 64-bit shared-memory kernel (128-bit sums)
 ])
 def test_polymat_full(p, n, d, log2n):
     g = W.SplitMix64(p ^ (n * 1000 + d))
