@@ -166,6 +166,29 @@ int polymul_mod_p_batch(const ntt_plan* plan, const void* d_a, size_t na,
                         const void* d_b, size_t nb, size_t batch, void* d_c,
                         unsigned schedule, void* d_ws, size_t ws_bytes, void* stream);
 
+/* Device staging bytes polymul_mod_p_batch_host needs for chunks of `chunk`
+ * products of na x nb words: two sets of one chunk's operands and result,
+ * plus the workspace of one chunk (0 on bad arguments). */
+size_t polymul_host_stage_size(const ntt_plan* plan, size_t na, size_t nb, size_t chunk);
+
+/* polymul_mod_p_batch (fused schedule; the products of Section 5.2) for
+ * operands and results in HOST memory: h_a is batch x na words, h_b batch x
+ * nb words, h_c receives batch x (na + nb - 1) words, laid out as for
+ * polymul_mod_p_batch.  The batch is cut into chunks of `chunk` products;
+ * the upload of one chunk, the product of the previous one (on `stream`)
+ * and the download of the one before run concurrently, through two library
+ * copy streams per device (created on the first call on that device and
+ * kept until exit).  Overlap needs page-locked host memory (cudaHostAlloc
+ * or cudaHostRegister); pageable memory gives the same result, slower.
+ * d_stage: caller-owned device memory of at least polymul_host_stage_size
+ * bytes for this chunk, 256-byte aligned; it and the host buffers are in
+ * use until the call's work on `stream` completes, which is also when h_c
+ * holds the result.  The plan's device must be current.  Errors as for
+ * polymul_mod_p_batch; NTT_ERR_WORKSPACE for a missing or short d_stage. */
+int polymul_mod_p_batch_host(const ntt_plan* plan, const void* h_a, size_t na, const void* h_b,
+                             size_t nb, size_t batch, void* h_c, size_t chunk, void* d_stage,
+                             size_t stage_bytes, void* stream);
+
 /* The single-product form of polymul_mod_p_batch (fused schedule). */
 int polymul_mod_p(const ntt_plan* plan, const void* d_a, size_t na, const void* d_b,
                   size_t nb, void* d_c, void* d_ws, size_t ws_bytes, void* stream);

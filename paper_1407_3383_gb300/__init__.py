@@ -99,6 +99,8 @@ def _load():
             "polymul_mod_p_batch": (_int, [_vp, _vp, _sz, _vp, _sz, _sz, _vp, _uint, _vp, _sz, _vp]),
             "polymul_mod_p": (_int, [_vp, _vp, _sz, _vp, _sz, _vp, _vp, _sz, _vp]),
             "polymul_mod_p_batch_static": (_int, [_vp, _vp, _sz, _vp, _sz, _sz, _vp, _vp]),
+            "polymul_host_stage_size": (_sz, [_vp, _sz, _sz, _sz]),
+            "polymul_mod_p_batch_host": (_int, [_vp, _vp, _sz, _vp, _sz, _sz, _vp, _sz, _vp, _sz, _vp]),
             "ntt_modmul_vec": (_int, [_u64, _uint, _uint, _vp, _vp, _vp, _vp, _sz, _vp]),
             "ntt_modmul_rate": (_int, [_u64, _uint, _uint, _int, ctypes.POINTER(ctypes.c_double)]),
             "polymat_workspace_size": (_sz, [_vp, _uint]),
@@ -534,16 +536,17 @@ def alloc_workspace(plan: Plan, batch: int, schedule: int = NTT_SCHED_FUSED, dev
     return torch.empty(nbytes, dtype=torch.uint8, device=device)
 
 
+def polymul_host_stage_size(plan: Plan, na: int, nb: int, chunk: int) -> int:
+    return int(_load().polymul_host_stage_size(plan.handle, na, nb, chunk))
+
+
 def polymul_mod_p_batch_host(plan: Plan, h_a, na: int, h_b, nb: int, batch: int, h_c,
-                             d_a, d_b, d_c, ws=None, stream=None):
-    """polymul_mod_p_batch on host operands: copy a, b (pinned host tensors)
-    to the device staging buffers d_a, d_b, run the product into d_c and copy
-    it back to h_c, all enqueued on `stream` (asynchronous)."""
-    import torch
-    st = torch.cuda.current_stream() if stream is None else stream
-    with torch.cuda.stream(st):
-        d_a[: batch * na].copy_(h_a[: batch * na], non_blocking=True)
-        d_b[: batch * nb].copy_(h_b[: batch * nb], non_blocking=True)
-        polymul_mod_p_batch(plan, d_a, na, d_b, nb, batch, d_c, NTT_SCHED_FUSED, ws, stream=st)
-        nc = batch * (na + nb - 1)
-        h_c[:nc].copy_(d_c[:nc], non_blocking=True)
+                             chunk: int, d_stage, stream=None):
+    """polymul_mod_p_batch on HOST operands (CPU tensors, page-locked for
+    overlap): the library uploads, multiplies and downloads in chunks of
+    `chunk` products on overlapping streams; d_stage is a device tensor of
+    polymul_host_stage_size bytes.  Asynchronous on `stream`."""
+    stage_bytes = d_stage.numel() * d_stage.element_size()
+    _check(_load().polymul_mod_p_batch_host(plan.handle, _ptr(h_a), na, _ptr(h_b), nb, batch,
+                                            _ptr(h_c), chunk, _ptr(d_stage), stage_bytes,
+                                            _stream(stream)), "polymul_mod_p_batch_host")

@@ -264,3 +264,41 @@ def test_tma_tiles_partial_rows(p, na, nb):
     assert (got == plain).all()
     assert (got == O.polymul_batch(p, a, b)).all()
 
+
+
+@pytest.mark.parametrize("p,log2n,na,nb,batch,chunk,pinned", [
+    (W.P_B, 16, 1 << 15, 1 << 15, 7, 3, True),     # ragged last chunk, three sets in flight
+    (W.P_B, 16, 1 << 15, 1 << 15, 4, 1, True),     # one product per chunk
+    (W.P_A, 12, 2048, 2048, 5, 64, False),          # chunk > batch, pageable host memory
+    (W.P2, 13, 4096, 4000, 6, 4, True),             # 64-bit words
+    (W.P_B, 15, 9000, 7001, 3, 2, True),            # two global passes with a workspace
+])
+def test_polymul_host_buffers(p, log2n, na, nb, batch, chunk, pinned):
+    """polymul_mod_p_batch_host (host operands, chunked copies overlapping
+    the products) returns the oracle's product for every pair, twice in a row
+    through the same staging buffer."""
+    import torch
+    a, b = W.pair_batch(p, batch, na, nb, seed=0x5EED0100 + log2n + chunk)
+    dt = torch.uint32 if p < 1 << 32 else torch.uint64
+    npt = np.uint32 if p < 1 << 32 else np.uint64
+
+    def host(x):
+        t = torch.from_numpy(np.ascontiguousarray(x.reshape(-1).astype(npt)))
+        return t.pin_memory() if pinned else t
+
+    ha, hb = host(a), host(b)
+    nc = na + nb - 1
+    with G.Plan(p, log2n) as plan:
+        stage = torch.empty(G.polymul_host_stage_size(plan, na, nb, chunk), dtype=torch.uint8,
+                            device="cuda")
+        for rep in range(2):
+            hc = torch.full((batch * nc,), 0xFFFF, dtype=dt)
+            hc = hc.pin_memory() if pinned else hc
+            G.polymul_mod_p_batch_host(plan, ha, na, hb, nb, batch, hc, chunk, stage)
+            torch.cuda.synchronize()
+            got = hc.numpy().astype(np.uint64).reshape(batch, nc)
+            for t in range(batch):
+                assert (got[t] == O.polymul(p, a[t], b[t])).all(), (rep, t)
+        with pytest.raises(G.NttError) as e:
+            G.polymul_mod_p_batch_host(plan, ha, na, hb, nb, batch, hc, chunk, stage[:256])
+        assert e.value.status == 10   # NTT_ERR_WORKSPACE
