@@ -53,7 +53,15 @@ struct Mont32 {
         const uint32_t m = static_cast<uint32_t>(d >> 32);
         return m * (0u - p) + static_cast<uint32_t>(d);
     }
-    __device__ __forceinline__ uint32_t add(uint32_t x, uint32_t y) const { return sub(x, p - y); }
+    // x + y rem p for x, y < p: z = x + y - p taken as a 64-bit two's
+    // complement value (x + y < 2^33) is negative exactly when x + y < p, so
+    // its high word is the mask and the correction is the same multiply-add.
+    // Two integer additions instead of the three of Function 4's x - (p - y).
+    __device__ __forceinline__ uint32_t add(uint32_t x, uint32_t y) const {
+        const uint64_t z = static_cast<uint64_t>(x) + y - p;
+        const uint32_t m = static_cast<uint32_t>(z >> 32);
+        return m * (0u - p) + static_cast<uint32_t>(z);
+    }
     // a difference that only feeds a twiddle product (any 32-bit input)
     __device__ __forceinline__ uint32_t sub_lazy(uint32_t x, uint32_t y) const { return sub(x, y); }
     // values are always fully reduced with this policy
