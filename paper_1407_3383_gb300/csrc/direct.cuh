@@ -120,7 +120,7 @@ k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long
             dif_regs<Ar, 16, ZHALF>(P.ar, x, P.rc);
 #pragma unroll
         for (int t = 1; t < 16; ++t)
-            if (!TFT || t < B) x[t] = P.ar.mulw(x[t], ltab[j1 * 16 + t]);
+            if (!TFT || t < B) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, ltab + j1 * 16 + t));
 #pragma unroll
         for (int t = 0; t < 16; ++t)
             if (!TFT || t < B) sm[(16 * t + j1) * kDCols + v] = x[t];
@@ -139,7 +139,7 @@ k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
             const long long pos = 16 * blk + t;
-            out[pos * kDLine] = P.ar.mulw(x[t], gt[pos * kDLine]);
+            out[pos * kDLine] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, gt + pos * kDLine));
         }
     }
 }
@@ -183,7 +183,7 @@ k_col_fwd_tma(DevPlan<Ar> P, const __grid_constant__ CUtensorMap map_a, const __
             dif_regs<Ar, 16, true>(P.ar, x, P.rc);
 #pragma unroll
         for (int t = 1; t < 16; ++t)
-            if (!TFT || t < B) x[t] = P.ar.mulw(x[t], ltab[j1 * 16 + t]);
+            if (!TFT || t < B) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, ltab + j1 * 16 + t));
 #pragma unroll
         for (int t = 0; t < 16; ++t)
             if (!TFT || t < B) sm[(16 * t + j1) * kDCols + v] = x[t];
@@ -202,7 +202,7 @@ k_col_fwd_tma(DevPlan<Ar> P, const __grid_constant__ CUtensorMap map_a, const __
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
             const long long pos = 16 * blk + t;
-            out[pos * kDLine] = P.ar.mulw(x[t], gt[pos * kDLine]);
+            out[pos * kDLine] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, gt + pos * kDLine));
         }
     }
 }
@@ -255,7 +255,7 @@ struct RowLayout {
 };
 
 constexpr int kDRowsPerBlock = 4;      // rows of each operand per row block (64 threads)
-constexpr int kDRowMinBlocks32 = 20;   // 32-bit words: 20 blocks per SM (48 registers, no spills)
+constexpr int kDRowMinBlocks32 = 16;   // 32-bit words: 16 blocks per SM (up to 64 registers)
 constexpr int kDNttRowsPerBlock = 8;   // standalone row transforms (128 threads)
 constexpr int kDTftMaxBlocks = 13;     // uniform batches needing more row blocks run the full kernels
 
@@ -285,7 +285,7 @@ k_row_polymul_d(DevPlan<Ar> P, typename Ar::word* __restrict__ ws, long long ws_
     word* base = ws + (prod_base + blockIdx.y) * ws_stride;
     const int j1 = threadIdx.x & 15, r = threadIdx.x >> 4;
     // outer forward pass of row r of operand i (line RPB i + r)
-    const tw* lf = P.line_fwd[kDLog];
+    const tw* lf = P.line256_t[0];
 #pragma unroll 1
     for (int i = 0; i < 2; ++i) {
         const word* in = base + i * N + static_cast<long long>(r0 + r) * kDLine + j1;
@@ -294,7 +294,7 @@ k_row_polymul_d(DevPlan<Ar> P, typename Ar::word* __restrict__ ws, long long ws_
         for (int t = 0; t < 16; ++t) x[t] = in[16 * t];
         dif_regs<Ar, 16>(P.ar, x, P.rc);
 #pragma unroll
-        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, lf + j1 * 16 + t));
+        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, lf + t * 16 + j1));
 #pragma unroll
         for (int t = 0; t < 16; ++t) sm[RL::at(RPB * i + r, 16 * t + j1)] = x[t];
     }
@@ -317,12 +317,12 @@ k_row_polymul_d(DevPlan<Ar> P, typename Ar::word* __restrict__ ws, long long ws_
     __syncthreads();
     // outer inverse pass of row r of the product
     {
-        const tw* li = P.line_inv[kDLog];
+        const tw* li = P.line256_t[1];
         word x[16];
 #pragma unroll
         for (int t = 0; t < 16; ++t) x[t] = sm[RL::at(r, 16 * t + j1)];
 #pragma unroll
-        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, li + j1 * 16 + t));
+        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, li + t * 16 + j1));
         dit_regs<Ar, 16>(P.ar, x, P.rci);
         word* o = base + static_cast<long long>(r0 + r) * kDLine + j1;
 #pragma unroll
@@ -347,12 +347,12 @@ k_row_ntt_d(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long prod_
     word* line = data + ((prod_base + blockIdx.y) << (2 * kDLog)) + static_cast<long long>(blockIdx.x * RPB + r) * kDLine;
     word x[16];
     if (FWD) {
-        const tw* lf = P.line_fwd[kDLog];
+        const tw* lf = P.line256_t[0];
 #pragma unroll
         for (int t = 0; t < 16; ++t) x[t] = line[16 * t + j1];
         dif_regs<Ar, 16>(P.ar, x, P.rc);
 #pragma unroll
-        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, lf + j1 * 16 + t));
+        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, lf + t * 16 + j1));
 #pragma unroll
         for (int t = 0; t < 16; ++t) sm[RL::at(r, 16 * t + j1)] = x[t];
         __syncthreads();
@@ -362,7 +362,7 @@ k_row_ntt_d(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long prod_
         for (int t = 0; t < 16; ++t) x[t] = P.ar.canon(x[t]);
         sm_store16(line + 16 * j1, x);
     } else {
-        const tw* li = P.line_inv[kDLog];
+        const tw* li = P.line256_t[1];
         sm_load16(line + 16 * j1, x);
         dit_regs<Ar, 16>(P.ar, x, P.rci);
         sm_store16(sm + RL::at(r, 16 * j1), x);
@@ -370,7 +370,7 @@ k_row_ntt_d(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long prod_
 #pragma unroll
         for (int t = 0; t < 16; ++t) x[t] = sm[RL::at(r, 16 * t + j1)];
 #pragma unroll
-        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, li + j1 * 16 + t));
+        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, li + t * 16 + j1));
         dit_regs<Ar, 16>(P.ar, x, P.rci);
 #pragma unroll
         for (int t = 0; t < 16; ++t) line[16 * t + j1] = x[t];

@@ -48,6 +48,9 @@ struct DevPlan {
     tw rci[8];                       // w_16^-e, e < 8
     const tw* line_fwd[kMaxLineLog + 1];   // [logM] (5..8): [j1*16 + t] = w_M^(j1 [t]_4)
     const tw* line_inv[kMaxLineLog + 1];
+    // the 256-point line tables transposed, [t*16 + j1] = w_256^(+-j1 [t]_4):
+    // lanes over j1 read consecutive entries (the direct row kernels)
+    const tw* line256_t[2];
     const tw* tile_fwd[17];          // [logT] (9..16): [r*L1 + c] = w_T^(c [r]_l2)
     const tw* tile_inv[17];
     const tw* glob_fwd;              // [j2*n1 + j1] = w_N^(j1 [j2]_k2)

@@ -253,7 +253,8 @@ void fill_outer_table(std::vector<uint64_t>& vals, uint64_t p, uint64_t w, int l
 template <class TwT, class Conv>
 static void build_tables(ntt_plan* P, TableBuilder<TwT>& tb, Conv conv,
                          size_t (&line_off)[2][kMaxLineLog + 1], size_t (&tile_off)[2][17],
-                         size_t (&glob_off)[3], size_t (&plain_off)[2], uint64_t pm_factor) {
+                         size_t (&glob_off)[3], size_t (&plain_off)[2], size_t (&linet_off)[2],
+                         uint64_t pm_factor) {
     const uint64_t p = P->p;
     const uint64_t g = P->g;
     auto root = [&](int logm, bool fwd) {
@@ -266,6 +267,7 @@ static void build_tables(ntt_plan* P, TableBuilder<TwT>& tb, Conv conv,
         for (int lm = 0; lm <= kMaxLineLog; ++lm) line_off[d][lm] = SIZE_MAX;
         for (int lt = 0; lt <= 16; ++lt) tile_off[d][lt] = SIZE_MAX;
         plain_off[d] = SIZE_MAX;
+        linet_off[d] = SIZE_MAX;
         if (fwd) glob_off[0] = glob_off[1] = glob_off[2] = SIZE_MAX;
         // radix-16 pass tables for sub-transform sizes 2^5 .. 2^8
         for (int lm = 5; lm <= kMaxLineLog && lm <= static_cast<int>(P->v2); ++lm) {
@@ -273,6 +275,12 @@ static void build_tables(ntt_plan* P, TableBuilder<TwT>& tb, Conv conv,
             const size_t off = tb.add(vals.size());
             for (size_t i = 0; i < vals.size(); ++i) tb.data[off + i] = conv(vals[i]);
             line_off[d][lm] = off;
+            if (lm == kMaxLineLog) {           // transposed copy: [t*16 + j1] = vals[j1*16 + t]
+                const size_t offt = tb.add(vals.size());
+                for (size_t j1 = 0; j1 < 16; ++j1)
+                    for (size_t t = 0; t < 16; ++t) tb.data[offt + t * 16 + j1] = conv(vals[j1 * 16 + t]);
+                linet_off[d] = offt;
+            }
         }
         // tile twiddles for every vector length above one line that the plan's kernels use
         std::vector<int> tiles;
@@ -351,8 +359,8 @@ static void build_tft(const ntt_plan* P, TftConsts<Ar>& K, Conv conv) {
 template <class Ar, class TwT, class Conv>
 static int finish_plan(ntt_plan* P, DevPlan<Ar>& dp, Conv conv, uint64_t pm_factor) {
     TableBuilder<TwT> tb;
-    size_t line_off[2][kMaxLineLog + 1], tile_off[2][17], glob_off[3], plain_off[2];
-    build_tables<TwT>(P, tb, conv, line_off, tile_off, glob_off, plain_off, pm_factor);
+    size_t line_off[2][kMaxLineLog + 1], tile_off[2][17], glob_off[3], plain_off[2], linet_off[2];
+    build_tables<TwT>(P, tb, conv, line_off, tile_off, glob_off, plain_off, linet_off, pm_factor);
     const uint64_t w16 = pow_mod(P->g, (P->p - 1) >> 4, P->p);
     const uint64_t w16i = pow_mod(w16, P->p - 2, P->p);
     for (int e = 0; e < 8; ++e) {
@@ -380,6 +388,8 @@ static int finish_plan(ntt_plan* P, DevPlan<Ar>& dp, Conv conv, uint64_t pm_fact
         dp.tile_fwd[lt] = at(tile_off[0][lt]);
         dp.tile_inv[lt] = at(tile_off[1][lt]);
     }
+    dp.line256_t[0] = at(linet_off[0]);
+    dp.line256_t[1] = at(linet_off[1]);
     dp.glob_fwd = at(glob_off[0]);
     dp.glob_inv = at(glob_off[1]);
     P->glob_inv_pm = at(glob_off[2]);
