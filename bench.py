@@ -437,7 +437,7 @@ def run_native(args, world, rank, local):
     hb = torch.from_numpy(b.reshape(-1)).pin_memory()
     hc = torch.empty(batch * nc, dtype=torch.uint32).pin_memory()
     e2e_steps = max(3, args.steps // 4)
-    chunks = sorted({c for c in (8, 16, 32, 64, batch) if c <= batch})
+    chunks = sorted({c for c in (16, 32, 48, 64, 80, 128, batch) if c <= batch})
     stage = torch.empty(max(G.polymul_host_stage_size(plan, na, nb, c) for c in chunks),
                         dtype=torch.uint8, device=dev)
 

@@ -167,14 +167,15 @@ int polymul_mod_p_batch(const ntt_plan* plan, const void* d_a, size_t na,
                         unsigned schedule, void* d_ws, size_t ws_bytes, void* stream);
 
 /* Device staging bytes polymul_mod_p_batch_host needs for chunks of `chunk`
- * products of na x nb words: two sets of one chunk's operands and result,
+ * products of na x nb words: three sets of one chunk's operands and result,
  * plus the workspace of one chunk (0 on bad arguments). */
 size_t polymul_host_stage_size(const ntt_plan* plan, size_t na, size_t nb, size_t chunk);
 
 /* polymul_mod_p_batch (fused schedule; the products of Section 5.2) for
  * operands and results in HOST memory: h_a is batch x na words, h_b batch x
  * nb words, h_c receives batch x (na + nb - 1) words, laid out as for
- * polymul_mod_p_batch.  The batch is cut into chunks of `chunk` products;
+ * polymul_mod_p_batch.  The batch is cut into chunks of at most `chunk`
+ * products (a long batch starts and ends with chunk/4 and chunk/2);
  * the upload of one chunk, the product of the previous one (on `stream`)
  * and the download of the one before run concurrently, through two library
  * copy streams per device (created on the first call on that device and

@@ -2,15 +2,16 @@
 //
 // polymul_mod_p_batch_host() runs the products of polymul_mod_p_batch (fused
 // schedule, Section 5.2) for operands and results that live in host memory.
-// The batch is cut into chunks of `chunk` products.  Chunk i is copied to
+// The batch is cut into chunks of at most `chunk` products (smaller at both
+// ends of a long batch, see chunk_sizes).  Chunk i is copied to
 // the device on a copy stream, multiplied on the caller's stream and copied
 // back on a second copy stream, so that the upload of chunk i+1, the product
-// of chunk i and the download of chunk i-1 run at the same time.  Two sets of
-// device staging buffers (operands and result of one chunk each) alternate
+// of chunk i and the download of chunk i-1 run at the same time.  Three sets
+// of device staging buffers (operands and result of one chunk each) rotate
 // between the chunks; one workspace serves the products, which run in order
 // on the caller's stream.  Events order the stages:
-//   upload(i)   after the product of chunk i-2 (it read the same operand set),
-//   product(i)  after upload(i) and after download(i-2) (same result set),
+//   upload(i)   after the product of chunk i-3 (it read the same operand set),
+//   product(i)  after upload(i) and after download(i-3) (same result set),
 //   download(i) after product(i),
 // and the caller's stream waits for the last download.
 //
@@ -20,8 +21,10 @@
 // event records.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/gbntt.h"
 #include "kernels.h"
@@ -30,7 +33,7 @@
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kSets = 2;
+constexpr int kSets = 3;
 
 struct CopyStreams {
     bool ready = false;
@@ -78,6 +81,30 @@ int ensure_streams(CopyStreams& cs) {
     }
     cs.ready = true;
     return NTT_OK;
+}
+
+// Chunk sizes for `batch` products with at most `chunk` per chunk.  The
+// first upload and the last product and download overlap nothing, so for
+// three or more full chunks the pipeline ramps: chunk/4, chunk/2, then full
+// chunks, then chunk/2 and chunk/4 (the remainder goes before the ramp-down).
+std::vector<size_t> chunk_sizes(size_t batch, size_t chunk) {
+    std::vector<size_t> v;
+    if (batch >= 3 * chunk && chunk >= 4) {
+        const size_t q = chunk / 4, h = chunk / 2;
+        v.push_back(q);
+        v.push_back(h);
+        size_t rem = batch - 2 * (q + h);
+        while (rem > chunk) {
+            v.push_back(chunk);
+            rem -= chunk;
+        }
+        v.push_back(rem);
+        v.push_back(h);
+        v.push_back(q);
+    } else {
+        for (size_t first = 0; first < batch; first += chunk) v.push_back(std::min(chunk, batch - first));
+    }
+    return v;
 }
 
 }  // namespace
@@ -139,11 +166,12 @@ extern "C" int polymul_mod_p_batch_host(const ntt_plan* plan, const void* h_a, s
         (e = cudaStreamWaitEvent(cs.down, cs.start, 0)) != cudaSuccess)
         return fail(e);
 
-    const size_t nchunks = (batch + chunk - 1) / chunk;
-    for (size_t i = 0; i < nchunks; ++i) {
+    const std::vector<size_t> sizes = chunk_sizes(batch, chunk);
+    const size_t nchunks = sizes.size();
+    size_t first = 0;
+    for (size_t i = 0; i < nchunks; first += sizes[i], ++i) {
         const int s = static_cast<int>(i % kSets);
-        const size_t first = i * chunk;
-        const size_t cnt = (batch - first < chunk) ? batch - first : chunk;
+        const size_t cnt = sizes[i];
         unsigned char* da = base + s * L.set;
         unsigned char* db = da + L.a;
         unsigned char* dc = db + L.b;

@@ -272,6 +272,7 @@ def test_tma_tiles_partial_rows(p, na, nb):
     (W.P_A, 12, 2048, 2048, 5, 64, False),          # chunk > batch, pageable host memory
     (W.P2, 13, 4096, 4000, 6, 4, True),             # 64-bit words
     (W.P_B, 15, 9000, 7001, 3, 2, True),            # two global passes with a workspace
+    (W.P_A, 12, 2048, 2048, 13, 4, True),           # ramped chunks 1, 2, 4, 3, 2, 1
 ])
 def test_polymul_host_buffers(p, log2n, na, nb, batch, chunk, pinned):
     """polymul_mod_p_batch_host (host operands, chunked copies overlapping
