@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -217,12 +218,15 @@ KERNEL_SOURCES = ["engine.cuh", "modarith.cuh", "tft.cuh", "direct.cuh", "subvec
 
 
 def source_hash() -> str:
-    """Hash of the sources that define the transform/product kernels."""
+    """Hash of the sources that define the transform/product kernels, with
+    line comments removed (a comment edit does not change a kernel)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1407_3383_gb300", "csrc")
     for name in KERNEL_SOURCES:
         h.update(name.encode())
-        h.update(open(os.path.join(csrc, name), "rb").read())
+        text = open(os.path.join(csrc, name), encoding="utf-8").read()
+        code = "\n".join(re.sub(r"//.*$", "", line).rstrip() for line in text.splitlines())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

@@ -17,9 +17,9 @@
 //    pointwise step) is Function 13 on the full product x y, giving
 //    x y 2^-32 rem p; the 2^32 is folded into the final scaling.
 //    Every correction is one subtraction with borrow: x - y rem p is
-//    d = x - y (mod 2^32) plus p when x < y.  Addition is Function 4's form
-//    x + y rem p = x - (p - y) (valid for m = n); the Montgomery tails
-//    hi(x w~) - hi(q p) are the same subtraction.  Sums and differences get
+//    d = x - y (mod 2^32) plus p when x < y.  Addition takes x + y - p as a
+//    64-bit value instead of Function 4's x - (p - y) (valid for m = n); the
+//    Montgomery tails hi(x w~) - hi(q p) are the same subtraction.  Sums and differences get
 //    the borrow as the high word of a 64-bit difference and add p with one
 //    multiply-add (FMA pipe); the tails use a compare and a select, the form
 //    that stays exact when both high products are equal.
