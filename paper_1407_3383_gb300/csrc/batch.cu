@@ -36,6 +36,7 @@ struct Bucket {
     unsigned first, count;
     ntt_plan* plan;
     size_t ws_off;
+    long long subs;      // 2^16-point row slots kept (products of 2^17 .. 2^24 points)
 };
 
 }  // namespace
@@ -193,9 +194,21 @@ int plan_products(polymul_batch_plan* B, const polymul_desc* h, size_t count, Tw
         bk.prime = h[big[s].idx].prime;
         bk.log2n = big[s].k;
         bk.first = static_cast<unsigned>(descs.size());
+        // products of 2^17 .. 2^24 points keep lam = ceil(L / 2^16) of their
+        // n2 = 2^(k-16) rows (whole blocks of n2/16 rows past 16 rows): the
+        // truncated transform of Section 5.1 with Algorithm 1's rows; their
+        // kept rows take consecutive slots of the bucket's workspace
+        const long long n2 = bk.log2n > 16 ? (1LL << (bk.log2n - 16)) : 0;
         while (s < big.size() && big[s].k == bk.log2n && h[big[s].idx].prime == bk.prime) {
             const polymul_desc& d = h[big[s].idx];
-            descs.push_back(BatchDesc{d.a_off, d.b_off, d.c_off, d.na, d.nb});
+            BatchDesc bd{d.a_off, d.b_off, d.c_off, d.na, d.nb, static_cast<unsigned long long>(bk.subs)};
+            if (n2) {
+                const long long L = static_cast<long long>(d.na) + d.nb - 1;
+                long long lam = std::min<long long>(n2, (L + 65535) >> 16);
+                if (n2 > 16) lam = (lam + n2 / 16 - 1) / (n2 / 16) * (n2 / 16);
+                bk.subs += lam;
+            }
+            descs.push_back(bd);
             ++bk.count;
             ++s;
         }
@@ -208,6 +221,8 @@ int plan_products(polymul_batch_plan* B, const polymul_desc* h, size_t count, Tw
         }
         bk.plan = B->big_plans[key];
         bk.ws_off = ws;
+        // sized for the untruncated schedule, which a tuned launch shape may
+        // select at run time (the kept rows need no more than that)
         ws = align256(ws + 2 * (size_t(1) << bk.log2n) * B->wb * bk.count);
         B->buckets.push_back(bk);
     }
@@ -251,10 +266,10 @@ int enqueue(polymul_batch_plan* B, const void* a, const void* b, void* c, void* 
         word* wsp = reinterpret_cast<word*>(wsb + bk.ws_off);
         if constexpr (sizeof(word) == 4)
             rc = launch_batch_bucket<Ar>(np, np->dp32, A, Bp, C, B->d_desc + bk.first, bk.count, wsp,
-                                         np->pm_scale32, s);
+                                         np->pm_scale32, s, bk.subs);
         else
             rc = launch_batch_bucket<Ar>(np, np->dp64, A, Bp, C, B->d_desc + bk.first, bk.count, wsp,
-                                         np->pm_scale64, s);
+                                         np->pm_scale64, s, bk.subs);
         if (rc != NTT_OK) return rc;
     }
     if (spread) {

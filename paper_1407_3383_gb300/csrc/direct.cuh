@@ -39,8 +39,11 @@ static_assert(kDItems * kDGroups == 16, "column blocks cover 16 x 16 lines");
 // Column blocks per SM the compiler must fit with 32-bit words: 4 leaves up
 // to 64 registers a thread, which measured 4% faster per product step than
 // the 32-48 the compiler picks unbounded (more loads in flight per thread).
-// 64-bit words would spill under that bound and keep the compiler's choice.
+// 64-bit words would spill under that bound; 2 blocks (up to 128 registers
+// instead of the 168 the compiler picks for the full column pass, which left
+// one block per SM) made their column pass 37% faster.
 constexpr int kDColMinBlocks = 4;
+constexpr int kDColMinBlocks64 = 2;   // 64-bit words: up to 128 registers
 
 __host__ __device__ constexpr size_t direct_col_smem_words() { return size_t(kDCols) * kDLine; }
 
@@ -81,7 +84,7 @@ __device__ __forceinline__ int dcol_rows(long long len, long long c) {
 // product length): the truncated Fourier transform of Section 5.1 with
 // Algorithm 1's rows, its outer 16-point pass truncated to B outputs.
 template <class Ar, bool ZHALF, bool TFT = false>
-__global__ void __launch_bounds__(kDThreads, sizeof(typename Ar::word) == 4 ? kDColMinBlocks : 1)
+__global__ void __launch_bounds__(kDThreads, sizeof(typename Ar::word) == 4 ? kDColMinBlocks : kDColMinBlocks64)
 k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long len0, long long sstride0,
             const typename Ar::word* __restrict__ src1, long long len1, long long sstride1,
             typename Ar::word* __restrict__ dst, long long dst_stride, long long dst_off1, long long prod_base,
@@ -261,6 +264,7 @@ struct RowLayout {
 
 constexpr int kDRowsPerBlock = 4;      // rows of each operand per row block (64 threads)
 constexpr int kDRowMinBlocks32 = 16;   // 32-bit words: 16 blocks per SM (up to 64 registers)
+constexpr int kDRowMinBlocks64 = 8;   // 64-bit words: up to 128 registers
 constexpr int kDNttRowsPerBlock = 8;   // standalone row transforms (128 threads)
 constexpr int kDTftMaxBlocks = 13;     // uniform batches needing more row blocks run the full kernels
 
@@ -273,7 +277,7 @@ __host__ __device__ constexpr size_t direct_ntt_row_smem_words() { return size_t
 // blocks keep the barrier-separated phases of neighbouring blocks apart.
 // TFT with descriptors: rows at or beyond the product's 16 B are not formed.
 template <class Ar, int RPB, bool TFT = false>
-__global__ void __launch_bounds__(RPB * 16, sizeof(typename Ar::word) == 4 ? kDRowMinBlocks32 : 1)
+__global__ void __launch_bounds__(RPB * 16, sizeof(typename Ar::word) == 4 ? kDRowMinBlocks32 : kDRowMinBlocks64)
 k_row_polymul_d(DevPlan<Ar> P, typename Ar::word* __restrict__ ws, long long ws_stride, long long prod_base,
                 const BatchDesc* __restrict__ desc) {
     using word = typename Ar::word;
@@ -390,7 +394,7 @@ k_row_ntt_d(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long prod_
 // (B known outputs, known zero inputs above them), scaled like the other
 // unnormalised passes.
 template <class Ar, bool TFT = false>
-__global__ void __launch_bounds__(kDThreads, sizeof(typename Ar::word) == 4 ? kDColMinBlocks : 1)
+__global__ void __launch_bounds__(kDThreads, sizeof(typename Ar::word) == 4 ? kDColMinBlocks : kDColMinBlocks64)
 k_col_inv_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src, long long src_stride,
             typename Ar::word* __restrict__ dst, long long out_len, long long dst_stride,
             const typename Ar::tw* __restrict__ itab, long long prod_base, const BatchDesc* __restrict__ desc,

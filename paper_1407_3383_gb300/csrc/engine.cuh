@@ -60,10 +60,13 @@ struct DevPlan {
 };
 
 // One product of an uneven batch: word offsets of its operands and output in
-// the batch's flat buffers, and the operand lengths.
+// the batch's flat buffers, and the operand lengths.  `sub`: for products of
+// 2^17 .. 2^24 points, the index of the product's first 2^16-point row slot
+// in its bucket's workspace (the rows the truncated transform keeps).
 struct BatchDesc {
     unsigned long long aoff, boff, coff;
     unsigned na, nb;
+    unsigned long long sub;
 };
 
 // A work item of the persistent kernel: `count` products (descriptors

@@ -35,7 +35,7 @@ template <class Ar>
 int launch_batch_bucket(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
                         const typename Ar::word* b, typename Ar::word* c, const BatchDesc* d_desc,
                         long long count, typename Ar::word* ws, typename Ar::tw scale,
-                        cudaStream_t st);
+                        cudaStream_t st, long long subs);
 
 template <class Ar>
 int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* data, long long batch,

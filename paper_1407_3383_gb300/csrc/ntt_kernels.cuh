@@ -974,13 +974,15 @@ int launch_sub_products(const ntt_plan* core, typename Ar::word* ws, long long c
 
 // Products of n = 2^17 .. 2^24 points (Algorithm 1 with n1 = 2^16): the pass
 // across the rows, the 2^16-point stage on the rows, the inverse pass.
-// Uniform batches keep only the rows their na + nb - 1 words need (TFT:
+// Every product keeps only the rows its na + nb - 1 words need (TFT:
 // lam = ceil((na + nb - 1) / 2^16), rounded up to whole R2-row blocks for
-// n2 > 16); uneven ones (desc) keep all n2.
+// n2 > 16).  Uneven batches (desc) take each product's lam from its
+// descriptor and its rows from slot desc.sub on; `subs` is the bucket's
+// total of kept rows, the number of 2^16-point sub-products.
 template <class Ar>
 int launch_polymul_sub(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a, long long na,
                        const typename Ar::word* b, long long nb, long long batch, typename Ar::word* c,
-                       typename Ar::word* ws, const BatchDesc* desc, cudaStream_t st) {
+                       typename Ar::word* ws, const BatchDesc* desc, cudaStream_t st, long long subs = 0) {
     using word = typename Ar::word;
     const int m = static_cast<int>(plan->log2n) - kSubLog;
     const int M = 1 << m;
@@ -992,7 +994,7 @@ int launch_polymul_sub(const ntt_plan* plan, const DevPlan<Ar>& dp, const typena
         B = (lam + R2 - 1) / R2;
         lam = B * R2;
     }
-    const bool tft = !desc && lam < M;
+    const bool tft = desc ? true : lam < M;
     const long long rows_stride = static_cast<long long>(lam) * 2 * kSubN;
     const auto* pre = static_cast<const typename Ar::tw*>(plan->pre_fwd);
     const auto* pre_inv = static_cast<const typename Ar::tw*>(plan->pre_inv);
@@ -1015,7 +1017,7 @@ int launch_polymul_sub(const ntt_plan* plan, const DevPlan<Ar>& dp, const typena
         }
         prof_mark(st, "k_pre_fwd");
     }
-    int rc = launch_sub_products<Ar>(plan->core, ws, batch * lam, st);
+    int rc = launch_sub_products<Ar>(plan->core, ws, desc ? subs : batch * lam, st);
     if (rc != NTT_OK) return rc;
     for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
@@ -1231,12 +1233,13 @@ template <class Ar>
 int launch_batch_bucket(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
                         const typename Ar::word* b, typename Ar::word* c, const BatchDesc* d_desc,
                         long long count, typename Ar::word* ws, typename Ar::tw scale,
-                        cudaStream_t st) {
+                        cudaStream_t st, long long subs) {
     using word = typename Ar::word;
     const int k = static_cast<int>(plan->log2n);
     const LaunchCfg cfg = launch_cfg(sizeof(word), k, plan->tile_max_log);
     if (cfg.logw == 0 && k == 2 * kDLog) return launch_polymul_direct<Ar>(plan, dp, a, 0, b, 0, count, c, ws, d_desc, st);
-    if (cfg.logw == 0 && plan->core) return launch_polymul_sub<Ar>(plan, dp, a, 0, b, 0, count, c, ws, d_desc, st);
+    if (cfg.logw == 0 && plan->core)
+        return launch_polymul_sub<Ar>(plan, dp, a, 0, b, 0, count, c, ws, d_desc, st, subs);
     const int k2 = plan->k2, k1 = plan->k1;
     const long long N = 1LL << k;
     const int logw = cfg.logw, lrpc = cfg.lrpc;

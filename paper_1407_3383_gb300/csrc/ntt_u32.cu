@@ -14,7 +14,7 @@ template int launch_batch_small<Mont32>(const DevPlan<Mont32>*, const BatchDesc*
                                          cudaStream_t);
 template int launch_batch_bucket<Mont32>(const ntt_plan*, const DevPlan<Mont32>&, const uint32_t*,
                                           const uint32_t*, uint32_t*, const BatchDesc*, long long,
-                                          uint32_t*, Tw32, cudaStream_t);
+                                          uint32_t*, Tw32, cudaStream_t, long long);
 template int batch_small_occupancy<Mont32>(size_t);
 template int launch_polymat<Mont32>(const ntt_plan*, const DevPlan<Mont32>&, const uint32_t*, const uint32_t*,
                                     int, long long, uint32_t*, uint32_t*, Tw32, Tw32, cudaStream_t);

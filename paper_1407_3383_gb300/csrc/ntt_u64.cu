@@ -14,7 +14,7 @@ template int launch_batch_small<Shoup64L>(const DevPlan<Shoup64L>*, const BatchD
                                          cudaStream_t);
 template int launch_batch_bucket<Shoup64L>(const ntt_plan*, const DevPlan<Shoup64L>&, const uint64_t*,
                                           const uint64_t*, uint64_t*, const BatchDesc*, long long,
-                                          uint64_t*, Tw64, cudaStream_t);
+                                          uint64_t*, Tw64, cudaStream_t, long long);
 template int batch_small_occupancy<Shoup64L>(size_t);
 template int launch_polymat<Shoup64L>(const ntt_plan*, const DevPlan<Shoup64L>&, const uint64_t*, const uint64_t*,
                                     int, long long, uint64_t*, uint64_t*, Tw64, Tw64, cudaStream_t);

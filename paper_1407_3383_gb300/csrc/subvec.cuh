@@ -25,7 +25,9 @@ constexpr int kSubThreads = 256;
 // Steps 1 and 2: read rows j2 < M of every product's operand (zero beyond
 // its length), M-point DIF across them (truncated to lam outputs with TFT),
 // twiddle, and write row j2 < lam to dst + prod*dprod + j2*dsub (+ doff1 for
-// operand b, blockIdx.z = 1).  In place when dst is the source.
+// operand b, blockIdx.z = 1).  In place when dst is the source.  With
+// descriptors and TFT, lam is the product's own ceil(L / 2^16) and its rows
+// start at slot d.sub: dst + (d.sub + j2)*dsub.
 template <class Ar, int M, bool TFT>
 __global__ void __launch_bounds__(kSubThreads)
 k_pre_fwd(Ar ar, DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long len0, long long sstride0,
@@ -37,11 +39,15 @@ k_pre_fwd(Ar ar, DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long
     const long long j1 = static_cast<long long>(blockIdx.x) * kSubThreads + threadIdx.x;
     const long long prod = prod_base + blockIdx.y;
     const word* src;
-    long long len;
+    long long len, first = prod * dprod;
     if (desc) {
         const BatchDesc d = desc[prod];
         src = blockIdx.z ? src1 + d.boff : src0 + d.aoff;
         len = blockIdx.z ? d.nb : d.na;
+        if (TFT) {
+            lam = static_cast<int>(std::min<long long>(M, (static_cast<long long>(d.na) + d.nb - 1 + kSubN - 1) / kSubN));
+            first = static_cast<long long>(d.sub) * dsub;
+        }
     } else {
         src = blockIdx.z ? src1 + prod * sstride1 : src0 + prod * sstride0;
         len = blockIdx.z ? len1 : len0;
@@ -56,7 +62,7 @@ k_pre_fwd(Ar ar, DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long
         tdif<Ar, M, 0>(ar, x, P.rc, lam);
     else
         dif_sub<Ar, M, 0>(ar, x, P.rc);
-    word* out = dst + prod * dprod + (blockIdx.z ? doff1 : 0) + j1;
+    word* out = dst + first + (blockIdx.z ? doff1 : 0) + j1;
 #pragma unroll
     for (int j2 = 0; j2 < M; ++j2)
         if (!TFT || j2 < lam) out[j2 * dsub] = ar.mulw(x[j2], pre[j2 * kSubN + j1]);
@@ -66,7 +72,8 @@ k_pre_fwd(Ar ar, DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long
 // (with n2^-1 folded into pre_inv), inverse M-point transform across the
 // rows (the inverse TFT with zero inputs above lam, with TFT), canonical
 // store of the first out_len words at dst + prod*dprod (or the descriptor's
-// offset and length).
+// offset and length; with descriptors and TFT the product's own lam and row
+// slots from d.sub, as in k_pre_fwd).
 template <class Ar, int M, bool TFT>
 __global__ void __launch_bounds__(kSubThreads)
 k_post_inv(Ar ar, DevPlan<Ar> P, TftConsts<Ar> K, const typename Ar::word* src, long long sprod, long long ssub,
@@ -75,14 +82,23 @@ k_post_inv(Ar ar, DevPlan<Ar> P, TftConsts<Ar> K, const typename Ar::word* src, 
     using word = typename Ar::word;
     const long long j1 = static_cast<long long>(blockIdx.x) * kSubThreads + threadIdx.x;
     const long long prod = prod_base + blockIdx.y;
-    const word* in = src + prod * sprod + j1;
+    long long first = prod * sprod;
+    if (desc && TFT) {
+        const BatchDesc d = desc[prod];
+        lam = static_cast<int>(std::min<long long>(M, (static_cast<long long>(d.na) + d.nb - 1 + kSubN - 1) / kSubN));
+        first = static_cast<long long>(d.sub) * ssub;
+    }
+    const word* in = src + first + j1;
     word x[16];
 #pragma unroll
     for (int j2 = 0; j2 < 16; ++j2) {
         x[j2] = word(0);
         if (j2 < M && (!TFT || j2 < lam)) x[j2] = ar.mulw(in[j2 * ssub], pre_inv[j2 * kSubN + j1]);
     }
-    if (TFT) {
+    if (TFT && lam >= M) {
+        // every row kept (uneven batches): the plain inverse, same residues
+        dit_sub<Ar, M, 0>(ar, x, P.rci);
+    } else if (TFT) {
         // the inverse TFT returns 16 times its inputs, which pre_inv scaled
         // by 1/M: multiply by M/16
         itft_z<Ar, M, 0>(ar, x, P.rc, P.rci, K, lam);
@@ -115,7 +131,8 @@ k_post_inv(Ar ar, DevPlan<Ar> P, TftConsts<Ar> K, const typename Ar::word* src, 
 // line table, an inner radix-R2 pass on blocks of R2 positions, then the
 // step-2 twiddle w_n^(c [pos]_C); position pos goes to dst + prod*dprod +
 // pos*dsub (+ doff1 for operand b).  32 columns per block.  ZHALF: rows at or
-// beyond n2/2 are zero.  TFT: only the first B of the 16 blocks are formed.
+// beyond n2/2 are zero.  TFT: only the first B of the 16 blocks are formed;
+// with descriptors, B is the product's own and its rows start at slot d.sub.
 template <class Ar, int C, bool ZHALF, bool TFT>
 __global__ void __launch_bounds__(kDThreads)
 k_colx_fwd(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long len0, long long sstride0,
@@ -130,7 +147,7 @@ k_colx_fwd(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long 
     const long long c = static_cast<long long>(blockIdx.x) * kDCols + v;
     const long long prod = prod_base + blockIdx.y;
     const word* src;
-    long long len;
+    long long len, first = prod * dprod;
     int B = 16;
     if (desc) {
         const BatchDesc d = desc[prod];
@@ -139,6 +156,7 @@ k_colx_fwd(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long 
         if (TFT) {
             const long long lam = (static_cast<long long>(d.na) + d.nb - 1 + kSubN - 1) / kSubN;
             B = static_cast<int>((lam + R2 - 1) / R2);
+            first = static_cast<long long>(d.sub) * dsub;
         }
     } else {
         src = blockIdx.z ? src1 + prod * sstride1 : src0 + prod * sstride0;
@@ -169,7 +187,7 @@ k_colx_fwd(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long 
             if (!TFT || t < B) sm[(R2 * t + j1) * kDCols + v] = x[t];
     }
     __syncthreads();
-    word* out = dst + prod * dprod + (blockIdx.z ? doff1 : 0) + c;
+    word* out = dst + first + (blockIdx.z ? doff1 : 0) + c;
 #pragma unroll
     for (int i = 0; i < kDItems; ++i) {
         const int blk = g + kDGroups * i;
@@ -204,19 +222,22 @@ k_colx_inv(DevPlan<Ar> P, TftConsts<Ar> K, const typename Ar::word* src, long lo
     const long long c = static_cast<long long>(blockIdx.x) * kDCols + v;
     const long long prod = prod_base + blockIdx.y;
     word* out;
-    long long len;
+    long long len, first = prod * sprod;
     int B = 16;
     if (desc) {
         const BatchDesc d = desc[prod];
         out = dst + d.coff;
         len = static_cast<long long>(d.na) + d.nb - 1;
-        if (TFT) B = static_cast<int>(((len + kSubN - 1) / kSubN + R2 - 1) / R2);
+        if (TFT) {
+            B = static_cast<int>(((len + kSubN - 1) / kSubN + R2 - 1) / R2);
+            first = static_cast<long long>(d.sub) * ssub;
+        }
     } else {
         out = dst + prod * dprod;
         len = out_len;
         if (TFT) B = beta;
     }
-    const word* in = src + prod * sprod + c;
+    const word* in = src + first + c;
 #pragma unroll
     for (int i = 0; i < kDItems; ++i) {
         const int blk = g + kDGroups * i;

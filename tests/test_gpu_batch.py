@@ -103,6 +103,34 @@ def test_uneven_batch_2e17_2e18_buckets(primes):
             assert int(got[t][k]) == O.poly_coeff(p, a_list[t], b_list[t], k)
 
 
+@pytest.mark.parametrize("primes", [[W.P1, W.P2], [W.P_B, W.P_A]])
+def test_uneven_batch_truncated_rows(primes):
+    """Uneven buckets of 2^17 .. 2^21 points keep each product's own row
+    count lam = ceil(L / 2^16) (whole blocks of n2/16 rows past 16 rows):
+    several products per bucket with different lam, equal to the padded
+    generic passes and to the oracle on sampled coefficients."""
+    g = W.SplitMix64(2121 + len(str(primes[0])))
+    la = [40000, 70000, 130000, 100000, 150000, 250000, 200000, 600000, 1000000, 70000]
+    lb = [30000, 70000, 130000, 40000, 150000, 250000, 100000, 500000, 1000000, 64000]
+    pidx = [0, 0, 0, 1, 0, 0, 0, 0, 0, 1]
+    a_list = [g.uniform_mod(primes[i], n) for i, n in zip(pidx, la)]
+    b_list = [g.uniform_mod(primes[i], n) for i, n in zip(pidx, lb)]
+    G.ntt_tune_reset()
+    got = _run_batch(primes, a_list, b_list, pidx)[0]
+    wb = 4 if primes[0] < (1 << 32) else 8
+    try:
+        G.ntt_tune_import("".join(f"{wb} {k} 0 {5 if wb == 4 else 4} 4\n" for k in (17, 18, 19, 21)))
+        padded = _run_batch(primes, a_list, b_list, pidx)[0]
+    finally:
+        G.ntt_tune_reset()
+    for t in range(len(la)):
+        assert (got[t] == padded[t]).all(), t
+        p = primes[pidx[t]]
+        n = got[t].size
+        for k in [0, n - 1, n // 3, (n * 5) // 7, 65535, 65536]:
+            assert int(got[t][k]) == O.poly_coeff(p, a_list[t], b_list[t], k), (t, k)
+
+
 def test_config3_full_workload_sampled():
     """10,000 products, lengths log-uniform in [2^6, 2^18], each modulo one
     of three 62-bit primes: sampled coefficients and fingerprints."""
