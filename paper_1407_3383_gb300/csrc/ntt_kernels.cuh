@@ -33,6 +33,8 @@
 namespace gbntt {
 
 constexpr int kThreads = 256;
+// shared memory above which a one-block product leaves room for one block per SM
+constexpr size_t kTileWideSmem = 114 * 1024;
 
 __host__ __device__ inline VecLayout tile_layout(int logL, int lognvec) {
     VecLayout L{};
@@ -78,8 +80,11 @@ __host__ __device__ inline long long slab_words(const VecLayout& L) {
 
 // ------------------------------------------------------------------ fused kernels
 
-template <class Ar>
-__global__ void __launch_bounds__(kThreads)
+// One block per product group, the whole product in shared memory.  NT
+// threads: tiles that leave room for one block per SM run 512 threads, so
+// that an SM holds 16 warps instead of 8.
+template <class Ar, int NT = kThreads>
+__global__ void __launch_bounds__(NT)
 k_tile_polymul(DevPlan<Ar> P, const typename Ar::word* __restrict__ a, long long na,
                const typename Ar::word* __restrict__ b, long long nb,
                typename Ar::word* __restrict__ c, long long batch, int logL, int lppc,
@@ -1130,12 +1135,14 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
     if (k <= plan->tile_max_log) {
         const int lppc = cfg.lppc;
         const size_t smem = layout_words(tile_layout(k, lppc + 1)) * sizeof(word);
-        if (allow_smem(k_tile_polymul<Ar>, smem) != cudaSuccess) return check_launch("smem attr");
+        const bool wide = smem > kTileWideSmem;
+        auto kt = wide ? k_tile_polymul<Ar, 2 * kThreads> : k_tile_polymul<Ar, kThreads>;
+        if (allow_smem(kt, smem) != cudaSuccess) return check_launch("smem attr");
         const long long blocks = (batch + (1LL << lppc) - 1) >> lppc;
         for (long long b0 = 0; b0 < blocks; b0 += 0x7fffffffLL) {
             const long long nb0 = std::min(blocks - b0, 0x7fffffffLL);
             const long long p0 = b0 << lppc;
-            k_tile_polymul<Ar><<<static_cast<unsigned>(nb0), kThreads, smem, st>>>(
+            kt<<<static_cast<unsigned>(nb0), wide ? 2 * kThreads : kThreads, smem, st>>>(
                 dp, a + p0 * na, na, b + p0 * nb, nb, c + p0 * (na + nb - 1), batch - p0, k, lppc,
                 scale);
             prof_mark(st, "k_tile_polymul");
