@@ -41,7 +41,7 @@ L2_BYTES = 129 * 1024 * 1024
 # 32-bit-instruction counts of the word policy's arithmetic (Mont32, any odd
 # p < 2^32): modular add, subtract, fixed-multiplicand product, general
 # (Montgomery) product.
-OPS32 = {"add": 4, "sub": 3, "mulw": 6, "mulg": 7}
+OPS32 = {"add": 3, "sub": 3, "mulw": 6, "mulg": 7}
 
 
 def parse():
