@@ -36,6 +36,22 @@ constexpr int kThreads = 256;
 // shared memory above which a one-block product leaves room for one block per SM
 constexpr size_t kTileWideSmem = 114 * 1024;
 
+// Multiprocessor count of a device, queried once per device (every caller
+// writes the same value, so concurrent first calls are harmless).
+inline int sm_count(int device) {
+    static int cache[64] = {};
+    if (device < 0 || device >= 64) return 1;
+    if (!cache[device]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 1;
+        }
+        cache[device] = n;
+    }
+    return cache[device];
+}
+
 __host__ __device__ inline VecLayout tile_layout(int logL, int lognvec) {
     VecLayout L{};
     L.logL = logL;
@@ -82,7 +98,9 @@ __host__ __device__ inline long long slab_words(const VecLayout& L) {
 
 // One block per product group, the whole product in shared memory.  NT
 // threads: tiles that leave room for one block per SM run 512 threads, so
-// that an SM holds 16 warps instead of 8.
+// that an SM holds 16 warps instead of 8; grids smaller than the GPU (a few
+// products, where each block has an SM to itself) run 1024 threads with
+// 32-bit words and 512 with 64-bit words.
 template <class Ar, int NT = kThreads>
 __global__ void __launch_bounds__(NT)
 k_tile_polymul(DevPlan<Ar> P, const typename Ar::word* __restrict__ a, long long na,
@@ -1135,14 +1153,22 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
     if (k <= plan->tile_max_log) {
         const int lppc = cfg.lppc;
         const size_t smem = layout_words(tile_layout(k, lppc + 1)) * sizeof(word);
-        const bool wide = smem > kTileWideSmem;
-        auto kt = wide ? k_tile_polymul<Ar, 2 * kThreads> : k_tile_polymul<Ar, kThreads>;
-        if (allow_smem(kt, smem) != cudaSuccess) return check_launch("smem attr");
         const long long blocks = (batch + (1LL << lppc) - 1) >> lppc;
+        const bool few = blocks < sm_count(plan->device);
+        const bool wide = few || smem > kTileWideSmem;
+        auto kt = wide ? k_tile_polymul<Ar, 2 * kThreads> : k_tile_polymul<Ar, kThreads>;
+        int nt = wide ? 2 * kThreads : kThreads;
+        if constexpr (sizeof(word) == 4) {
+            if (few) {
+                kt = k_tile_polymul<Ar, 4 * kThreads>;
+                nt = 4 * kThreads;
+            }
+        }
+        if (allow_smem(kt, smem) != cudaSuccess) return check_launch("smem attr");
         for (long long b0 = 0; b0 < blocks; b0 += 0x7fffffffLL) {
             const long long nb0 = std::min(blocks - b0, 0x7fffffffLL);
             const long long p0 = b0 << lppc;
-            kt<<<static_cast<unsigned>(nb0), wide ? 2 * kThreads : kThreads, smem, st>>>(
+            kt<<<static_cast<unsigned>(nb0), nt, smem, st>>>(
                 dp, a + p0 * na, na, b + p0 * nb, nb, c + p0 * (na + nb - 1), batch - p0, k, lppc,
                 scale);
             prof_mark(st, "k_tile_polymul");
