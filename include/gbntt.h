@@ -185,7 +185,9 @@ size_t polymul_host_stage_size(const ntt_plan* plan, size_t na, size_t nb, size_
  * bytes for this chunk, 256-byte aligned; it and the host buffers are in
  * use until the call's work on `stream` completes, which is also when h_c
  * holds the result.  The plan's device must be current.  Errors as for
- * polymul_mod_p_batch; NTT_ERR_WORKSPACE for a missing or short d_stage. */
+ * polymul_mod_p_batch; NTT_ERR_WORKSPACE for a missing or short d_stage.
+ * Argument errors return before anything is enqueued; a CUDA runtime error
+ * while enqueueing (NTT_ERR_CUDA) can leave earlier chunks enqueued. */
 int polymul_mod_p_batch_host(const ntt_plan* plan, const void* h_a, size_t na, const void* h_b,
                              size_t nb, size_t batch, void* h_c, size_t chunk, void* d_stage,
                              size_t stage_bytes, void* stream);
