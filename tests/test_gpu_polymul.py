@@ -303,3 +303,38 @@ def test_polymul_host_buffers(p, log2n, na, nb, batch, chunk, pinned):
         with pytest.raises(G.NttError) as e:
             G.polymul_mod_p_batch_host(plan, ha, na, hb, nb, batch, hc, chunk, stage[:256])
         assert e.value.status == 10   # NTT_ERR_WORKSPACE
+
+
+def test_polymul_host_buffers_edge_cases():
+    """polymul_mod_p_batch_host: an empty batch is a no-op; a zero chunk, a
+    length past n and a staging buffer sized for a smaller chunk are refused
+    before anything is enqueued; doubles (NTT_FLAG_FP64 plans) take the same
+    path and match the integer plan's product."""
+    import torch
+    p = W.P_TABLE12
+    a, b = W.pair_batch(p, 5, 1500, 1000, seed=0x5EED0200)
+    with G.Plan(p, 12) as plan:
+        stage = torch.empty(G.polymul_host_stage_size(plan, 1500, 1000, 2), dtype=torch.uint8, device="cuda")
+        ha = torch.from_numpy(a.reshape(-1).astype(np.uint64)).pin_memory()
+        hb = torch.from_numpy(b.reshape(-1).astype(np.uint64)).pin_memory()
+        hc = torch.zeros(5 * 2499, dtype=torch.uint64).pin_memory()
+        G.polymul_mod_p_batch_host(plan, ha, 1500, hb, 1000, 0, hc, 2, stage)      # empty batch
+        torch.cuda.synchronize()
+        assert int(hc.sum()) == 0
+        for chunk, na, st, status in [(0, 1500, stage, 1), (2, 3500, stage, 5), (4, 1500, stage, 10)]:
+            with pytest.raises(G.NttError) as e:
+                G.polymul_mod_p_batch_host(plan, ha, na, hb, 1000, 5, hc, chunk, st)
+            assert e.value.status == status, (chunk, na)
+        G.polymul_mod_p_batch_host(plan, ha, 1500, hb, 1000, 5, hc, 2, stage)
+        torch.cuda.synchronize()
+        want = hc.numpy().copy().reshape(5, 2499)
+    for t in range(5):
+        assert (want[t] == O.polymul(p, a[t], b[t])).all(), t
+    with G.Plan(p, 12, G.NTT_FLAG_FP64) as plan:
+        stage = torch.empty(G.polymul_host_stage_size(plan, 1500, 1000, 2), dtype=torch.uint8, device="cuda")
+        ha = torch.from_numpy(a.reshape(-1).astype(np.float64)).pin_memory()
+        hb = torch.from_numpy(b.reshape(-1).astype(np.float64)).pin_memory()
+        hc = torch.zeros(5 * 2499, dtype=torch.float64).pin_memory()
+        G.polymul_mod_p_batch_host(plan, ha, 1500, hb, 1000, 5, hc, 2, stage)
+        torch.cuda.synchronize()
+        assert (hc.numpy().astype(np.uint64).reshape(5, 2499) == want).all()
