@@ -197,21 +197,25 @@ int polymul_mod_p(const ntt_plan* plan, const void* d_a, size_t na, const void* 
                   size_t nb, void* d_c, void* d_ws, size_t ws_bytes, void* stream);
 
 /* polymul_mod_p_batch with the fused schedule for callers that cannot
- * allocate device memory when they need a product: code running while a
- * stream is captured into a CUDA graph, host callbacks on a stream (which
- * may not call the CUDA API), latency-critical loops that cannot afford an
- * allocation's implicit synchronisation, and hosts that own all device
- * memory through their own allocator.  The paper has no counterpart (its
- * products run on the CPU).  Operands and output are as for
- * polymul_mod_p_batch; the scratch space the larger transforms need comes
- * from a fixed 32 MiB array inside the library (held on every GPU that loads
- * the library until the process exits), so this call allocates nothing.
- * Products needing more scratch than that (2 n word_bytes per product when
- * n > 2^tile_max_log) return NTT_ERR_WORKSPACE.  The first call on each
- * device looks up the array's address and must come before any stream
- * capture.  Every call shares the one array: calls whose work overlaps on
- * the GPU race and must be serialised by the caller.  The plan's device
- * must be current. */
+ * allocate device memory when they need a product: hosts that own all
+ * device memory through their own allocator or a budget fixed at start-up,
+ * and latency-critical loops that cannot take an allocation's implicit
+ * synchronisation or the risk of its failing mid-run.  The paper has no
+ * counterpart (its products run on the CPU).  Operands and output are as
+ * for polymul_mod_p_batch; the scratch space the larger transforms need
+ * comes from a fixed 32 MiB array inside the library (held on every GPU
+ * that loads the library until the process exits), so this call allocates
+ * nothing.  Products needing more scratch than that (2 n word_bytes per
+ * product when n > 2^tile_max_log: at most 64 products of n = 2^16 with
+ * 32-bit words, 32 with 64-bit words) return NTT_ERR_WORKSPACE.  The first
+ * call on each device (and the first after that device's context changes,
+ * e.g. after cudaDeviceReset) looks up the array's address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * Every call shares the one array, which keeps the last call's contents:
+ * calls whose work overlaps on the GPU race and must be serialised by the
+ * caller.  A plan created with NTT_FLAG_CHECK copies the operands to the
+ * host and synchronises the stream on every call, as polymul_mod_p_batch
+ * does.  The plan's device must be current. */
 int polymul_mod_p_batch_static(const ntt_plan* plan, const void* d_a, size_t na,
                                const void* d_b, size_t nb, size_t batch, void* d_c,
                                void* stream);

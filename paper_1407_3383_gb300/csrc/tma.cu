@@ -32,7 +32,33 @@ EncodeTiledFn encoder() {
     return fn;
 }
 
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
 }  // namespace
+
+unsigned long long current_context_id() {
+    static std::once_flag once;
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+        cudaGetLastError();
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
 
 bool encode_tensor_map_3d(CUtensorMap* map, CUtensorMapDataType type, void* base, const uint64_t dims[3],
                           const uint64_t strides_bytes[2], const uint32_t box[3]) {
@@ -49,16 +75,19 @@ bool encode_tensor_map_3d(CUtensorMap* map, CUtensorMapDataType type, void* base
 int* device_error_flag() {
     static std::mutex mu;
     static int* by_device[64] = {};
+    static unsigned long long ctx_of[64] = {};   // context the cached address belongs to
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
     std::lock_guard<std::mutex> lock(mu);
-    if (!by_device[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!by_device[dev] || ctx == 0 || ctx != ctx_of[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
         by_device[dev] = static_cast<int*>(p);
+        ctx_of[dev] = current_context_id();   // the look-up makes the context current
     }
     return by_device[dev];
 }

@@ -82,4 +82,10 @@ bool encode_tensor_map_3d(CUtensorMap* map, CUtensorMapDataType type, void* base
 // Host: the device address of the error flag on the current device.
 int* device_error_flag();
 
+// Host: a process-unique id of the calling thread's current CUDA context
+// (cuCtxGetId), 0 when no context is current.  Addresses of __device__
+// variables belong to one context: a cache of them keyed by this id is
+// refreshed after a device reset creates a new one.
+unsigned long long current_context_id();
+
 }  // namespace gbntt

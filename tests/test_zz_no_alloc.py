@@ -1,12 +1,14 @@
 """polymul_mod_p_batch_static: the product entry point that allocates nothing.
 
 It exists for callers that cannot allocate device memory when they need a
-product (during CUDA graph capture, inside stream callbacks, in loops that
-cannot take an allocation's implicit synchronisation, or under a host
-application's own allocator).  It must give exactly what polymul_mod_p_batch
-gives with a caller-allocated workspace.  This file is collected last so a
-failure here cannot hide failures elsewhere; it also passes when run alone in
-a fresh process (the first call performs the one-time scratch set-up)."""
+product: hosts that own all device memory through their own allocator or a
+fixed budget, and latency-critical loops that cannot take an allocation's
+implicit synchronisation.  It must give exactly what polymul_mod_p_batch
+gives with a caller-allocated workspace, on two calls in a row, and a call
+after the first must leave the device's free memory unchanged.  This file is
+collected last so a failure here cannot hide failures elsewhere; it also
+passes when run alone in a fresh process (the first call performs the
+one-time scratch set-up)."""
 import numpy as np
 import pytest
 
@@ -39,8 +41,12 @@ def test_static_scratch_matches_workspace_entry(p, log2n, na, nb, batch):
             c_ref = empty_dev(batch * (na + nb - 1), wb)
             c_static = empty_dev(batch * (na + nb - 1), wb)
             G.polymul_mod_p_batch(plan, da, na, db, nb, batch, c_ref, G.NTT_SCHED_FUSED, ws)
+            torch.cuda.synchronize()
+            free_before = torch.cuda.mem_get_info()[0]
             G.polymul_mod_p_batch_static(plan, da, na, db, nb, batch, c_static)
             torch.cuda.synchronize()
+            if call:                                # after the first call's set-up
+                assert torch.cuda.mem_get_info()[0] == free_before, "the call allocated device memory"
             ref = from_dev(c_ref)
             got = from_dev(c_static)
             assert (got == ref).all(), f"call {call}"
