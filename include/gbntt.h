@@ -432,10 +432,13 @@ int ntt_profile_begin(void);
 int ntt_profile_end(int max_kernels, float* ms_out, const char** names_out, int* count);
 
 /* Integer-pipe throughput probe: `blocks` x `threads` threads run
- * independent chains of 32-bit multiply-adds (kind 0) or of adds/xors
- * (kind 1), 64 * iters operations each; writes operations per second to
- * *ops_per_s (timed with CUDA events on `stream`; synchronous).  Allocates
- * a small device buffer. */
+ * independent chains of 32-bit multiply-adds (kind 0), of adds/xors
+ * (kind 1), of both interleaved 1:1 (kind 2: the issue ceiling of integer
+ * work split evenly over the multiply-add and ALU pipes, the roof of the
+ * transform kernels), or of 32 x 32 -> 64-bit multiply-adds (kind 3),
+ * 64 * iters operations each; writes operations per second to *ops_per_s
+ * (timed with CUDA events on `stream`; synchronous).  Not part of the
+ * paper: a measurement of the machine.  Allocates a small device buffer. */
 int ntt_int_probe(unsigned kind, int blocks, int threads, int iters, void* stream,
                   double* ops_per_s);
 

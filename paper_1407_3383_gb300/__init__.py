@@ -43,6 +43,10 @@ NTT_BATCH_GRAPH = 2
 NTT_REQ_INTMUL = 0
 NTT_REQ_POLYMUL = 1
 NTT_REQ_DEVICE = 0x1
+NTT_PROBE_IMAD = 0
+NTT_PROBE_ALU = 1
+NTT_PROBE_MIXED = 2
+NTT_PROBE_WIDE = 3
 
 _lock = threading.Lock()
 _lib = None
@@ -116,6 +120,10 @@ def _load():
             "ntt_tune_import": (_int, [ctypes.c_char_p]),
             "ntt_tune_reset": (_int, []),
             "ntt_device_status": (_int, []),
+            "ntt_int_probe": (_int, [_uint, _int, _int, _int, _vp, ctypes.POINTER(ctypes.c_double)]),
+            "ntt_profile_begin": (_int, []),
+            "ntt_profile_end": (_int, [_int, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_char_p),
+                                       ctypes.POINTER(_int)]),
             "ntt_server_create": (_int, [_vp, ctypes.POINTER(_vp)]),
             "ntt_server_submit": (_int, [_vp, _uint, _uint, _vp, _sz, _vp, _sz, _vp, _uint,
                                          ctypes.POINTER(_u64)]),
@@ -513,6 +521,28 @@ def ntt_modmul_rate(p: int, kind: int, word_bytes: int, iters: int = 2048) -> fl
     out = ctypes.c_double()
     _check(_load().ntt_modmul_rate(p, kind, word_bytes, iters, ctypes.byref(out)), "ntt_modmul_rate")
     return out.value
+
+
+def ntt_int_probe(kind: int, blocks: int, threads: int = 256, iters: int = 4096, stream=None) -> float:
+    """Integer operations per second of the throughput probe `kind`
+    (NTT_PROBE_IMAD, _ALU, _MIXED or _WIDE); synchronous."""
+    out = ctypes.c_double()
+    _check(_load().ntt_int_probe(kind, blocks, threads, iters, _stream(stream), ctypes.byref(out)),
+           "ntt_int_probe")
+    return out.value
+
+
+def ntt_profile_begin():
+    _check(_load().ntt_profile_begin(), "ntt_profile_begin")
+
+
+def ntt_profile_end(cap: int = 256) -> list[tuple[str, float]]:
+    """(kernel name, device ms) of every launch since ntt_profile_begin()."""
+    ms = (ctypes.c_float * cap)()
+    names = (ctypes.c_char_p * cap)()
+    cnt = ctypes.c_int()
+    _check(_load().ntt_profile_end(cap, ms, names, ctypes.byref(cnt)), "ntt_profile_end")
+    return [(names[i].decode(), float(ms[i])) for i in range(min(cnt.value, cap))]
 
 
 def intmat_workspace_size(plan: IntmulPlan, n: int, na: int, nb: int) -> int:

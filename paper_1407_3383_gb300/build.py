@@ -80,5 +80,23 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+GEN_SRC = os.path.join(HERE, "workloads_gen.c")
+GEN_LIB = os.path.join(BUILD, "libworkloads.so")
+
+
+def build_generator(force: bool = False) -> str:
+    """The input generators' C stream (workloads_gen.c) as a host library."""
+    if not force and os.path.exists(GEN_LIB) and os.path.getmtime(GEN_LIB) >= os.path.getmtime(GEN_SRC):
+        return GEN_LIB
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = GEN_LIB + f".tmp{os.getpid()}"
+    r = subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-o", tmp, GEN_SRC], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"gcc failed on {GEN_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, GEN_LIB)
+    return GEN_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build_generator(force="--force" in sys.argv))

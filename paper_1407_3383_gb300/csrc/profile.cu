@@ -63,53 +63,70 @@ void prof_begin_call(cudaStream_t st) {
     }
 }
 
-// Integer throughput probe: independent chains of 32-bit multiply-adds
-// (IMAD) or of add/xor (ALU) per thread; every result feeds a store.
+// Integer throughput probe, 64 operations per thread per iteration on
+// independent chains, every result feeding a store:
+//   kind 0  32-bit multiply-adds (the multiply-add pipe);
+//   kind 1  add and xor alternating along each chain (the ALU pipe);
+//   kind 2  both at once, 1:1 -- eight multiply-add chains interleaved with
+//           eight add/xor chains, so that each pipe has independent work
+//           whenever the other is busy: the issue ceiling when integer work
+//           splits evenly between the two pipes;
+//   kind 3  32 x 32 -> 64-bit multiply-adds into 64-bit accumulators.
+#define GB_MAD(x) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x) : "r"(m), "r"(c))
+#define GB_ADD(x) asm volatile("add.u32 %0, %0, %1;" : "+r"(x) : "r"(m))
+#define GB_XOR(x) asm volatile("xor.b32 %0, %0, %1;" : "+r"(x) : "r"(c))
+#define GB_WIDE(x) asm volatile("{\n .reg .u32 lo;\n cvt.u32.u64 lo, %0;\n mad.wide.u32 %0, lo, %1, %0;\n}" \
+                                : "+l"(x) : "r"(m))
+#define GB_8(OP, a) OP(a##0); OP(a##1); OP(a##2); OP(a##3); OP(a##4); OP(a##5); OP(a##6); OP(a##7)
+
 __global__ void k_int_probe(uint32_t* out, int iters, int kind, uint32_t seed) {
     uint32_t a0 = threadIdx.x ^ seed, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
     uint32_t a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+    uint32_t b0 = a0 ^ 0x55u, b1 = b0 + 1, b2 = b0 + 2, b3 = b0 + 3;
+    uint32_t b4 = b0 + 4, b5 = b0 + 5, b6 = b0 + 6, b7 = b0 + 7;
     const uint32_t m = seed | 1u, c = seed >> 3;
     if (kind == 0) {
         for (int i = 0; i < iters; ++i) {
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a0) : "r"(m), "r"(c));
-                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a1) : "r"(m), "r"(c));
-                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a2) : "r"(m), "r"(c));
-                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a3) : "r"(m), "r"(c));
-                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a4) : "r"(m), "r"(c));
-                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a5) : "r"(m), "r"(c));
-                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a6) : "r"(m), "r"(c));
-                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a7) : "r"(m), "r"(c));
-            }
+            for (int u = 0; u < 8; ++u) { GB_8(GB_MAD, a); }
         }
-    } else {
+    } else if (kind == 1) {
         // add and xor alternate along each chain so no two consecutive
         // operations can merge into one three-input instruction
         for (int i = 0; i < iters; ++i) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                asm volatile("add.u32 %0, %0, %1;" : "+r"(a0) : "r"(m));
-                asm volatile("add.u32 %0, %0, %1;" : "+r"(a1) : "r"(m));
-                asm volatile("add.u32 %0, %0, %1;" : "+r"(a2) : "r"(m));
-                asm volatile("add.u32 %0, %0, %1;" : "+r"(a3) : "r"(m));
-                asm volatile("add.u32 %0, %0, %1;" : "+r"(a4) : "r"(m));
-                asm volatile("add.u32 %0, %0, %1;" : "+r"(a5) : "r"(m));
-                asm volatile("add.u32 %0, %0, %1;" : "+r"(a6) : "r"(m));
-                asm volatile("add.u32 %0, %0, %1;" : "+r"(a7) : "r"(m));
-                asm volatile("xor.b32 %0, %0, %1;" : "+r"(a0) : "r"(c));
-                asm volatile("xor.b32 %0, %0, %1;" : "+r"(a1) : "r"(c));
-                asm volatile("xor.b32 %0, %0, %1;" : "+r"(a2) : "r"(c));
-                asm volatile("xor.b32 %0, %0, %1;" : "+r"(a3) : "r"(c));
-                asm volatile("xor.b32 %0, %0, %1;" : "+r"(a4) : "r"(c));
-                asm volatile("xor.b32 %0, %0, %1;" : "+r"(a5) : "r"(c));
-                asm volatile("xor.b32 %0, %0, %1;" : "+r"(a6) : "r"(c));
-                asm volatile("xor.b32 %0, %0, %1;" : "+r"(a7) : "r"(c));
+                GB_8(GB_ADD, a);
+                GB_8(GB_XOR, a);
             }
         }
+    } else if (kind == 2) {
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                GB_8(GB_MAD, a);
+                GB_8(GB_ADD, b);
+                GB_8(GB_MAD, a);
+                GB_8(GB_XOR, b);
+            }
+        }
+    } else {
+        uint64_t w0 = a0, w1 = a1, w2 = a2, w3 = a3, w4 = a4, w5 = a5, w6 = a6, w7 = a7;
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) { GB_8(GB_WIDE, w); }
+        }
+        a0 = static_cast<uint32_t>(w0 ^ w1 ^ w2 ^ w3 ^ (w4 >> 32) ^ (w5 >> 32) ^ (w6 >> 32) ^ (w7 >> 32));
     }
-    out[blockIdx.x * blockDim.x + threadIdx.x] = a0 ^ a1 ^ a2 ^ a3 ^ a4 ^ a5 ^ a6 ^ a7;
+    out[blockIdx.x * blockDim.x + threadIdx.x] = a0 ^ a1 ^ a2 ^ a3 ^ a4 ^ a5 ^ a6 ^ a7 ^
+                                                 b0 ^ b1 ^ b2 ^ b3 ^ b4 ^ b5 ^ b6 ^ b7;
 }
+
+#undef GB_8
+#undef GB_WIDE
+#undef GB_XOR
+#undef GB_ADD
+#undef GB_MAD
 
 }  // namespace gbntt
 
@@ -150,7 +167,7 @@ extern "C" int ntt_profile_end(int max_kernels, float* ms_out, const char** name
 
 extern "C" int ntt_int_probe(unsigned kind, int blocks, int threads, int iters, void* stream,
                              double* ops_per_s) {
-    if (!ops_per_s || blocks <= 0 || threads <= 0 || iters <= 0 || kind > 1) return NTT_ERR_ARG;
+    if (!ops_per_s || blocks <= 0 || threads <= 0 || iters <= 0 || kind > 3) return NTT_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint32_t* out = nullptr;
     if (cudaMalloc(&out, sizeof(uint32_t) * static_cast<size_t>(blocks) * threads) != cudaSuccess)

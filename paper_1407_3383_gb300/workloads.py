@@ -27,9 +27,29 @@ Configurations (seed = 0x5EED0000 + index):
 """
 from __future__ import annotations
 
+import ctypes
 import math
+import os
 
 import numpy as np
+
+_GEN_LIB = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libworkloads.so")
+_gen = None
+
+
+def _gen_lib():
+    """workloads_gen.c (the same stream in C, for speed), or None when it is
+    not built; the numpy code below gives identical draws."""
+    global _gen
+    if _gen is None:
+        _gen = False
+        if os.path.exists(_GEN_LIB):
+            lib = ctypes.CDLL(_GEN_LIB)
+            u64p = ctypes.POINTER(ctypes.c_uint64)
+            lib.wl_u64.argtypes = [u64p, ctypes.c_void_p, ctypes.c_size_t]
+            lib.wl_uniform_mod.argtypes = [u64p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_size_t]
+            _gen = lib
+    return _gen or None
 
 SEED_BASE = 0x5EED0000
 _GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -50,11 +70,22 @@ P3 = 2305940865748566017
 class SplitMix64:
     """splitmix64 stream; every method advances the same state."""
 
-    def __init__(self, seed: int):
+    def __init__(self, seed: int, native: bool = True):
         self.state = np.uint64(seed & 0xFFFFFFFFFFFFFFFF)
+        self.native = native
+
+    def _c(self):
+        return _gen_lib() if self.native else None
 
     def u64(self, n: int) -> np.ndarray:
         n = int(n)
+        lib = self._c()
+        if lib is not None:
+            out = np.empty(n, dtype=np.uint64)
+            st = ctypes.c_uint64(int(self.state))
+            lib.wl_u64(ctypes.byref(st), out.ctypes.data, n)
+            self.state = np.uint64(st.value)
+            return out
         with np.errstate(over="ignore"):
             idx = np.arange(1, n + 1, dtype=np.uint64)
             z = self.state + idx * _GAMMA
@@ -68,6 +99,13 @@ class SplitMix64:
         """n residues uniform in [0, p), by rejection of the top partial block."""
         n = int(n)
         p = int(p)
+        lib = self._c()
+        if lib is not None and p > 1 and p % 2:
+            out = np.empty(n, dtype=np.uint64)
+            st = ctypes.c_uint64(int(self.state))
+            lib.wl_uniform_mod(ctypes.byref(st), p, out.ctypes.data, n)
+            self.state = np.uint64(st.value)
+            return out
         limit = np.uint64(((1 << 64) // p) * p - 1)   # accept draws <= limit
         out = np.empty(n, dtype=np.uint64)
         filled = 0
