@@ -44,6 +44,23 @@ L2_BYTES = 129 * 1024 * 1024
 OPS32 = {"add": 3, "sub": 3, "mulw": 6, "mulg": 7}
 
 
+# 32-bit-instruction counts of the 64-bit word policy's forms (Shoup64L,
+# p < 2^62, lazy residues in [0, 2p)), from their decomposition into 32-bit
+# instructions: a 64-bit add or subtract is 2 (low word with carry, high
+# word); a 64-bit unsigned compare 2; a 64-bit select 2; the low 64 bits of
+# a 64 x 64 product 3 (one wide multiply and two multiply-adds into the high
+# word); the high 64 bits 6 (the high word of the low partial product, three
+# wide multiply-adds with 64-bit addends, one 64-bit add).
+#   add      red2(x + y): add 2, then s - 2p, compare, select: 8
+#   sub      red2(x + 2p - y) (one three-input add per word): 8
+#   sub_lazy x + 2p - y, feeding a twiddle product: 2
+#   mulw     Function 8: high product 6, two low products 6, subtract 2: 14
+#   mulg     Montgomery: 128-bit product 8, q = lo p' 3, high product 6,
+#            subtract 2, compare 2, corrected select 4: 25
+#   canon    [0, 2p) -> [0, p): compare 2, subtract 2, select 2: 6
+OPS64 = {"add": 8, "sub": 8, "sub_lazy": 2, "mulw": 14, "mulg": 25, "canon": 6}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -65,6 +82,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per stream")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape (profiler captures)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the other workloads (single product, 64-bit transform and products, "
+                         "uneven batch, serving) that the default N=1 line carries")
     return ap.parse_args()
 
 
@@ -103,6 +123,28 @@ def fused_kernel_ops(log2n: int, na: int, nb: int, batch: int, tile_max_log: int
     ops.update({name + "_d": v for name, v in ops.items()})
     ops["k_col_fwd_tma"] = ops["k_col_fwd"]            # the same pass with its input tile by TMA
     return ops
+
+
+def transform_ops64(L: int) -> int:
+    """64-bit-word transform of length L on the radix-2 network: every
+    butterfly has a sum; differences that feed a twiddle product are lazy."""
+    o = OPS64
+    nt, tr = dif_counts(L)
+    return nt * (o["add"] + o["sub_lazy"] + o["mulw"]) + tr * (o["add"] + o["sub"])
+
+
+def ntt64_ops(L: int, batch: int = 1) -> int:
+    """One forward (or inverse, its scaling folded into a twiddle table)
+    transform per vector, canonical output words."""
+    return batch * (transform_ops64(L) + L * OPS64["canon"])
+
+
+def polymul64_ops(log2n: int, na: int, nb: int, batch: int) -> int:
+    """Products with 64-bit words: three transforms, n pointwise products,
+    the final scaling and canonical store of every output word."""
+    o = OPS64
+    n, nc = 1 << log2n, na + nb - 1
+    return batch * (3 * transform_ops64(n) + n * o["mulg"] + nc * (o["mulw"] + o["canon"]))
 
 
 def alg_bytes(na, nb, batch, wb):
@@ -258,11 +300,11 @@ def time_oracle(p, a, b, target_s: float = 12.0):
     one = time.perf_counter() - t0
     count = int(max(1, min(a.shape[0], target_s / max(one, 1e-6))))
     t0 = time.perf_counter()
-    O.polymul_batch(p, a[:count].astype(np.uint64), b[:count].astype(np.uint64))
+    prods = O.polymul_batch(p, a[:count].astype(np.uint64), b[:count].astype(np.uint64))
     dt = time.perf_counter() - t0
     sample = (f"{count} of the {a.shape[0]} products (schoolbook, all {a.shape[1] + b.shape[1] - 1} "
               f"coefficients each), {dt:.1f} s wall on {cores} threads")
-    return count / dt, cores, sample
+    return count / dt, cores, sample, prods
 
 
 def run_reference(args, world, rank, target_s: float = 120.0):
@@ -378,6 +420,249 @@ def profile_window(G, step, flush, steps):
     return per, launches / max(1, steps)
 
 
+def measured_hbm_gbs() -> float:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)).get("hbm_gbs", 6800.0)
+    return 6800.0
+
+
+def measure_probes(G, stream) -> dict:
+    """Integer operations/s of each probe kind (G op/s)."""
+    out = {}
+    for kind, name in [(G.NTT_PROBE_IMAD, "imad"), (G.NTT_PROBE_ALU, "iadd_lop"),
+                       (G.NTT_PROBE_MIXED, "mixed"), (G.NTT_PROBE_WIDE, "imad_wide")]:
+        try:
+            out[name + "_gops"] = round(G.ntt_int_probe(kind, SM_COUNT * 8, 256, 4096, stream) / 1e9, 1)
+        except Exception:
+            pass
+    return out
+
+
+def alu_roofline(ops: float, seconds: float, peak_gops: float) -> dict:
+    ach = ops / seconds / 1e9
+    return {"bound": "alu", "achieved": ach, "peak": peak_gops, "unit": "Gop/s", "frac": ach / peak_gops,
+            "alg_gop": ops / 1e9}
+
+
+def hbm_roofline(nbytes: float, seconds: float, hbm: float) -> dict:
+    ach = nbytes / seconds / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "alg_bytes": nbytes}
+
+
+def run_workloads(G, dev, stream, flush, peak_gops: float, hbm: float) -> dict:
+    """The workloads other than the headline, each with its own config and
+    rooflines: one 4096-point product (latency), one 2^24-point transform and
+    1024 products of 2^12 words mod a 62-bit prime, the 10,000-product uneven
+    batch against one library call per product, and a closed-loop serving
+    run.  Device time with CUDA events on the launching stream, L2 flushed
+    before each timed repetition; every result is checked (against the
+    oracle, a round trip, or another schedule)."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_1407_3383_gb300 import workloads as W
+    res = {}
+
+    def med(step, reps, warm=3):
+        for _ in range(warm):
+            step()
+        torch.cuda.synchronize()
+        return statistics.median(timed_steps(step, flush, reps, stream))
+
+    # -- one product of two length-2048 operands mod 998244353 (4096 points)
+    t0 = time.perf_counter()
+    p, a, b = W.config0()
+    with G.Plan(p, 12) as plan:
+        da = torch.from_numpy(a.astype(np.uint32)).to(dev)
+        db = torch.from_numpy(b.astype(np.uint32)).to(dev)
+        dc = torch.empty(4095, dtype=torch.uint32, device=dev)
+        ms = med(lambda: G.polymul_mod_p(plan, da, 2048, db, 2048, dc, stream=stream), 50)
+        ok = bool((dc.cpu().numpy().astype(np.uint64) == O.polymul(p, a, b)).all())
+        side = torch.cuda.Stream(device=dev)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            G.polymul_mod_p(plan, da, 2048, db, 2048, dc, stream=side)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(graph, stream=side):
+                for _ in range(100):
+                    G.polymul_mod_p(plan, da, 2048, db, 2048, dc, stream=side)
+        gms = med(lambda: graph.replay(), 10)
+        ops = fused_kernel_ops(12, 2048, 2048, 1, plan.info.tile_max_log)["k_tile_polymul"]
+        res["single_product"] = {
+            "config": {"workload": "1 product 2048 x 2048 mod 998244353 (119*2^23+1), 4096-point NTTs, u32",
+                       "l2": "flushed before each call"},
+            "metric": "latency per product", "value": 1e3 * ms, "unit": "us", "higher_is_better": False,
+            "graph_replayed_products_per_s": 100 / (gms * 1e-3),
+            "roofline": dict(alu_roofline(ops, ms * 1e-3, peak_gops), bound="latency",
+                             note="one thread block on one of 152 SMs"),
+            "matches_oracle": ok, "wall_s": time.perf_counter() - t0}
+
+    # -- one 2^24-point transform mod P1, forward then inverse
+    t0 = time.perf_counter()
+    p, x = W.config2_transform()
+    with G.Plan(p, 24) as plan:
+        dx = torch.from_numpy(x).to(dev)
+        fms = med(lambda: G.ntt_forward(plan, dx, 1, stream=stream), 10)
+        ims = med(lambda: G.ntt_inverse(plan, dx, 1, stream=stream), 10)
+        ok = bool((dx.cpu().numpy() == x).all())          # equal numbers of forwards and inverses
+        n = 1 << 24
+        ops = 2 * ntt64_ops(n)
+        nbytes = 2 * 2 * n * 8                              # each transform reads and writes n words once
+        sec = (fms + ims) * 1e-3
+        res["transform_2e24_u64"] = {
+            "config": {"workload": "one 2^24-point transform mod P1 = 2097222*2^40+1 (62-bit), forward then "
+                                   "inverse, u64", "l2": "flushed before each transform"},
+            "metric": "forward + inverse time", "value": fms + ims, "unit": "ms", "higher_is_better": False,
+            "forward_ms": fms, "inverse_ms": ims,
+            "roofline": alu_roofline(ops, sec, peak_gops), "hbm": hbm_roofline(nbytes, sec, hbm),
+            "round_trip_exact": ok, "wall_s": time.perf_counter() - t0}
+        del dx
+
+    # -- 1024 products of length 2^12 mod P1 (2^13 points, u64)
+    t0 = time.perf_counter()
+    p, a, b = W.config2_products()
+    with G.Plan(p, 13) as plan:
+        da = torch.from_numpy(a.reshape(-1)).to(dev)
+        db = torch.from_numpy(b.reshape(-1)).to(dev)
+        dc = torch.empty(1024 * 8191, dtype=torch.uint64, device=dev)
+        ms = med(lambda: G.polymul_mod_p_batch(plan, da, 4096, db, 4096, 1024, dc, stream=stream), 20)
+        sel = [0, 511, 1023]
+        want = O.polymul_batch(p, a[sel], b[sel])
+        ok = bool((dc.view(1024, 8191)[sel].cpu().numpy() == want).all())
+        ops = polymul64_ops(13, 4096, 4096, 1024)
+        nbytes = 1024 * (2 * 4096 + 8191) * 8
+        res["products_2e12_u64"] = {
+            "config": {"workload": "1024 products 2^12 x 2^12 mod P1 (62-bit), 2^13-point NTTs, u64",
+                       "l2": "flushed before each call"},
+            "metric": "products/s", "value": 1024 / (ms * 1e-3), "unit": "products/s", "higher_is_better": True,
+            "ms": ms, "roofline": alu_roofline(ops, ms * 1e-3, peak_gops),
+            "hbm": hbm_roofline(nbytes, ms * 1e-3, hbm),
+            "oracle_checked_products": len(sel), "matches_oracle": ok, "wall_s": time.perf_counter() - t0}
+        del da, db, dc
+
+    # -- 10,000 uneven products mod P1..P3, against one library call per product
+    t0 = time.perf_counter()
+    res["uneven_10000"] = uneven_batch(G, dev, stream, flush, med)
+    res["uneven_10000"]["wall_s"] = time.perf_counter() - t0
+
+    # -- serving: closed-loop stream of integer products
+    t0 = time.perf_counter()
+    res["serving"] = serve_closed_loop(G, requests=48)
+    res["serving"]["wall_s"] = time.perf_counter() - t0
+    return res
+
+
+def uneven_batch(G, dev, stream, flush, med) -> dict:
+    """The 10,000-product uneven batch (lengths log-uniform in [2^6, 2^18],
+    modulus uniform over P1..P3) in its three run modes, and the same
+    products as one polymul_mod_p call per product (its own plan per modulus
+    and power-of-two size, issued back to back from the host)."""
+    import ctypes
+    import numpy as np
+    import torch
+    from paper_1407_3383_gb300 import workloads as W
+    lengths, pidx = W.config3_shapes()
+    _, al, bl = W.config3_operands(lengths, pidx)
+    primes = [W.P1, W.P2, W.P3]
+    count = len(al)
+    with G.BatchPlan(primes, [v.size for v in al], [v.size for v in bl], pidx) as bp:
+        a = torch.from_numpy(np.concatenate(al)).to(dev)
+        b = torch.from_numpy(np.concatenate(bl)).to(dev)
+        del al, bl
+        c = torch.empty(bp.c_words, dtype=torch.uint64, device=dev)
+        ws = torch.empty(bp.workspace_size(), dtype=torch.uint8, device=dev)
+        modes = {}
+        for mode, nm in [(G.NTT_BATCH_DIRECT, "direct"), (G.NTT_BATCH_STREAMS, "streams"),
+                         (G.NTT_BATCH_GRAPH, "graph")]:
+            modes[nm + "_ms"] = med(lambda: bp.run(a, b, c, ws, mode, stream=stream), 5, warm=2)
+        # one call per product
+        L = np.asarray(lengths, dtype=np.int64)
+        logn = np.array([max(1, int(2 * v - 2).bit_length()) for v in L])   # ceil(log2(2 L - 1))
+        plans = {}
+        for pi, k in set(zip(pidx.tolist(), logn.tolist())):
+            plans[(pi, k)] = G.Plan(primes[pi], k)
+        ws1 = max(G.polymul_workspace_size(pl, 1) for pl in plans.values())
+        wsp = torch.empty(max(ws1, 256), dtype=torch.uint8, device=dev)
+        c2 = torch.empty_like(c)
+        offa = np.concatenate([[0], np.cumsum(L)[:-1]]) * 8
+        offc = np.concatenate([[0], np.cumsum(2 * L - 1)[:-1]]) * 8
+        lib = G.lib()
+        fn = lib.polymul_mod_p
+        st = stream.cuda_stream
+        calls = [(plans[(int(pidx[t]), int(logn[t]))].handle, a.data_ptr() + int(offa[t]), int(L[t]),
+                  b.data_ptr() + int(offa[t]), int(L[t]), c2.data_ptr() + int(offc[t])) for t in range(count)]
+        wp, wb_ = wsp.data_ptr(), wsp.numel()
+
+        def per_product():
+            for h, pa, la, pb, lb, pc in calls:
+                rc = fn(h, pa, la, pb, lb, pc, wp, wb_, st)
+                if rc:
+                    raise G.NttError(rc, "polymul_mod_p")
+
+        loop_ms = med(per_product, 3, warm=1)
+        same = bool(torch.equal(c, c2))
+        for pl in plans.values():
+            pl.close()
+        del a, b, c, c2, ws, wsp
+    best = min(modes.values())
+    return {"config": {"workload": "10,000 products, lengths log-uniform in [2^6, 2^18] (both operands), "
+                                   "modulus uniform over three 62-bit primes k*2^40+1, u64",
+                       "l2": "flushed before each run"},
+            "metric": "products/s", "value": count / (modes["graph_ms"] * 1e-3), "unit": "products/s",
+            "higher_is_better": True, **modes,
+            "per_product_calls_ms": loop_ms,
+            "per_product_note": "one polymul_mod_p call per product, back to back on one stream from a "
+                                "Python loop over prebuilt ctypes arguments (power-of-two sizes, no TFT)",
+            "batched_over_per_product": loop_ms / modes["graph_ms"],
+            "best_mode_products_per_s": count / (best * 1e-3),
+            "per_product_equals_batched": same}
+
+
+def serve_closed_loop(G, requests: int = 48) -> dict:
+    """A closed-loop run of the serving loop: `requests` integer products
+    (operand bits log-uniform in [2^14, 2^28]) submitted at once after a
+    warm-up pass; products/s and p50/p99 latency."""
+    import numpy as np
+    import torch
+    from paper_1407_3383_gb300 import workloads as W
+    _, limbs = W.config4_requests(requests, rate=1.0)
+    g = W.SplitMix64(W.SEED_BASE + 4 + (1 << 32))
+    reqs = []
+    for n in limbs:
+        n = int(n)
+        reqs.append((torch.from_numpy(g.limbs(n)).pin_memory(), torch.from_numpy(g.limbs(n)).pin_memory(),
+                     torch.empty(2 * n, dtype=torch.uint32).pin_memory()))
+    srv = G.Server(max_limbs=int(limbs.max()), mem_bytes=8 << 30, slots=4)
+
+    def burst():
+        start = time.perf_counter()
+        ids = [srv.submit(G.NTT_REQ_INTMUL, a, b, c) for a, b, c in reqs]
+        lat = []
+        for rid in ids:
+            lat.append(srv.wait(rid, 600000))
+            srv.release(rid)
+        return np.array(lat), time.perf_counter() - start
+
+    burst()
+    lat, span = burst()
+    # one request checked against Python integers (the product of the limbs)
+    k = int(np.argmin(limbs))
+    a, b, c = reqs[k]
+    to_int = lambda v: int.from_bytes(v.numpy().astype("<u4").tobytes(), "little")
+    ok = to_int(c) == to_int(a) * to_int(b)
+    stats = srv.stats()
+    srv.close()
+    return {"config": {"workload": f"closed loop of {requests} integer products, operand bits log-uniform in "
+                                   "[2^14, 2^28], three 62-bit primes, minimal-d chunks (80-91 bits), CRT + carry",
+                       "slots": 4, "arena_gib": 8, "mean_bits": float(limbs.mean() * 32)},
+            "metric": "integer products/s", "value": requests / span, "unit": "products/s",
+            "higher_is_better": True, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "peak_inflight": stats["peak_inflight"],
+            "checked_smallest_request": ok}
+
+
 def run_native(args, world, rank, local):
     import numpy as np
     import torch
@@ -456,9 +741,6 @@ def run_native(args, world, rank, local):
     dom = max(shares, key=shares.get)
     dom_ms = statistics.mean(per_kernel[dom])
     dom_ops = kops.get(dom, 0)
-    sm_mhz = clk["sm_mhz"] or SM_MAX_MHZ
-    peak_gops = SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e9
-    achieved_gops = dom_ops / (dom_ms * 1e-3) / 1e9
 
     # ---- plain schedule, same inputs
     psteps = args.plain_steps or max(3, args.steps // 4)
@@ -495,27 +777,38 @@ def run_native(args, world, rank, local):
     e2e_value = whole_job_value(batch, world, e2e_seconds(e2e_chunk, e2e_steps))
     e2e_ok = bool((hc.numpy() == dc.cpu().numpy()).all())
 
-    # int-pipe probe (context for the roofline)
-    probe = {}
-    import ctypes
-    lib = G.lib()
-    for kind, name in [(0, "imad"), (1, "iadd_lop")]:
-        out = ctypes.c_double()
-        lib.ntt_int_probe.argtypes = [ctypes.c_uint, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
-        if lib.ntt_int_probe(kind, SM_COUNT * 8, 256, 4096, stream.cuda_stream,
-                             ctypes.byref(out)) == 0:
-            probe[name + "_gops"] = round(out.value / 1e9, 1)
+    # ---- fused and plain give the same words (dc holds the plain result)
+    plain_out = dc.clone()
+    step_fused()
+    torch.cuda.synchronize()
+    fused_equals_plain = bool(torch.equal(dc, plain_out))
+    del plain_out
+
+    # ---- integer-issue probes: the roof of the integer-bound kernels
+    probe = measure_probes(G, stream)
+    peak_gops = probe.get("mixed_gops") or SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e-3
+    peak_basis = ("measured: ntt_int_probe mixed kind (independent 32-bit multiply-add and add/xor chains "
+                  "1:1, 152 x 8 blocks of 256 threads), this run" if probe.get("mixed_gops") else
+                  "152 SMs x 128 int32 lanes x 2070 MHz (unit counts and max clock; the probe failed)")
+    achieved_gops = dom_ops / (dom_ms * 1e-3) / 1e9
 
     bytes_step = alg_bytes(na, nb, batch, wb)
-    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs") \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    hbm = measured_hbm_gbs()
     gbps = bytes_step / (ms_per_step * 1e-3) / 1e9
+
+    # ---- the other workloads (N = 1 line only)
+    workloads = None
+    if world == 1 and not args.no_workloads:
+        workloads = run_workloads(G, dev, stream, flush, peak_gops, hbm)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cv, cores, sample = time_oracle(p, a, b)
-        cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        import numpy as np
+        cv, cores, sample, prods = time_oracle(p, a, b)
+        got = dc.view(batch, nc)[:prods.shape[0]].cpu().numpy().astype(np.uint64)
+        cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+               "parity_checked_products": int(prods.shape[0]),
+               "parity_ok": bool((got == prods).all())}
 
     if rank != 0:
         plan.close()
@@ -534,9 +827,10 @@ def run_native(args, world, rank, local):
                   "fused_over_plain": value / plain_value},
         "roofline": {"bound": "alu", "achieved": achieved_gops, "peak": peak_gops,
                      "unit": "Gop/s", "frac": achieved_gops / peak_gops, "traffic": traffic,
-                     "kernel": dom, "kernel_ms": dom_ms,
-                     "peak_basis": "152 SMs x 128 int32 lanes x 2070 MHz (unit counts and max clock)",
+                     "kernel": dom, "kernel_ms": dom_ms, "peak_basis": peak_basis,
+                     "unit_count_peak_gops": SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e-3,
                      "int_probe": probe},
+        "fused_equals_plain": fused_equals_plain,
         "kernels": {k: {"ms_mean": statistics.mean(v), "share": shares[k] / sum(shares.values()),
                         "alg_gop_per_launch": kops.get(k, 0) / 1e9} for k, v in per_kernel.items()},
         "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -548,6 +842,7 @@ def run_native(args, world, rank, local):
                 "matches_device_result": e2e_ok},
         "clocks": clk,
         "cpu_baseline": cpu,
+        "workloads": workloads,
     }
     print(json.dumps(line), flush=True)
     plan.close()
@@ -613,7 +908,7 @@ def run_serve(args, world, rank, local):
             "value": sat, "unit": "products/s", "n_gpus": world, "higher_is_better": True,
             "data": "synthetic", "dtype": "u64",
             "config": {"workload": f"Poisson stream of {len(reqs)} integer products, operand bits "
-                                   "log-uniform in [2^14, 2^28], 3 primes k*2^40+1, h = 64",
+                                   "log-uniform in [2^14, 2^28], 3 primes k*2^40+1, minimal-d chunks (80-91 bits)",
                        "mean_bits": float(bits.mean()), "max_bits": int(bits.max()),
                        "slots": 4, "arena_gib": 24},
             "runs": runs, "peak_inflight": stats["peak_inflight"], "server_setup_s": setup_s,

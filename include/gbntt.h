@@ -340,7 +340,10 @@ int ntt_autotune(const ntt_plan* plan, size_t batch, void* stream, float* best_m
  * columns per block and rows per block, each as log2.  For n = 2^16 .. 2^24
  * above the one-block limit, logw = 0 (the default) selects the direct
  * kernels, whose block shape is fixed (lrpc is then ignored); at n = 2^16,
- * lppc = 1 makes them bring zero-half operand tiles in by TMA. */
+ * lppc = 1 makes them bring zero-half operand tiles in by TMA.  The
+ * autotuner never picks that shape (a block whose bounded TMA waits both
+ * expire would return with its copy still in flight); it is set only
+ * through ntt_tune_import. */
 int ntt_tune_get(unsigned word_bytes, unsigned log2n, int* lppc, int* logw, int* lrpc);
 /* Forget every tuned or imported shape (back to the defaults). */
 int ntt_tune_reset(void);

@@ -191,11 +191,11 @@ extern "C" int ntt_autotune(const ntt_plan* plan, size_t batch, void* stream, fl
             if (t < g_t) g_t = t, g = cfg;
         }
         if (g_t < best_t) best_t = g_t, best = g;
-        if (k == 2 * kDLog) {                          // direct kernels with TMA input tiles
-            LaunchCfg t{1, 0, 0};
-            const float tt = try_cfg(t);
-            if (tt < best_t) best_t = tt, best = t;
-        }
+        // The direct kernels with TMA input tiles (lppc = 1 at n = 2^16) are
+        // not a candidate: a block whose bounded waits both expire returns
+        // with its bulk copy possibly still writing the block's shared
+        // memory, and no bounded exit avoids that.  They time the same as
+        // the per-thread loads and stay available through ntt_tune_import.
     }
     set_launch_cfg(wb, k, best);
     if (best_ms) *best_ms = best_t;

@@ -70,3 +70,21 @@ def test_product_kernel_totals():
 
 def test_algorithmic_bytes():
     assert bench.alg_bytes(1 << 15, 1 << 15, 256, 4) == 256 * ((1 << 15) * 2 + (1 << 16) - 1) * 4
+
+
+def test_u64_counts():
+    """The 64-bit forms: a butterfly whose difference feeds a twiddle product
+    costs a sum, a lazy difference and a twiddle product; the others a sum
+    and a full difference; products add three transforms, the pointwise
+    products and the scaled canonical store."""
+    o = bench.OPS64
+    for k in range(1, 14):
+        L = 1 << k
+        nt, tr = bench.dif_counts(L)
+        assert bench.transform_ops64(L) == nt * (o["add"] + o["sub_lazy"] + o["mulw"]) + tr * (o["add"] + o["sub"])
+        assert bench.ntt64_ops(L, 3) == 3 * (bench.transform_ops64(L) + L * o["canon"])
+    n, na, nb = 1 << 13, 4096, 4096
+    assert bench.polymul64_ops(13, na, nb, 2) == 2 * (3 * bench.transform_ops64(n) + n * o["mulg"]
+                                                      + (na + nb - 1) * (o["mulw"] + o["canon"]))
+    # per radix-2 butterfly: within the 20-24 32-bit operations estimated for 64-bit words
+    assert 20 <= o["add"] + o["sub_lazy"] + o["mulw"] <= 24

@@ -113,3 +113,29 @@ def test_oversized_request_is_rejected():
         with pytest.raises(G.NttError) as e:
             srv.submit(G.NTT_REQ_INTMUL, a, a, c)
         assert e.value.status == 5
+
+
+def test_wait_times_out_on_a_pending_request():
+    """ntt_server_wait with a time limit shorter than the request returns
+    NTT_ERR_TIMEOUT (a host-side wait: nothing on the GPU is made to hang);
+    the request still completes correctly afterwards, and a request that is
+    not finished cannot be released."""
+    import torch
+    g = W.SplitMix64(17)
+    n = 1 << 21
+    bufs = [(torch.from_numpy(g.limbs(n)).pin_memory(), torch.from_numpy(g.limbs(n)).pin_memory(),
+             torch.zeros(2 * n, dtype=torch.uint32).pin_memory()) for _ in range(3)]
+    with G.Server(max_limbs=n, mem_bytes=4 << 30, slots=1) as srv:
+        ids = [srv.submit(G.NTT_REQ_INTMUL, ta, tb, tc) for ta, tb, tc in bufs]
+        with pytest.raises(G.NttError) as e:      # the last one queues behind two others
+            srv.wait(ids[-1], 0)
+        assert e.value.status == 8                # NTT_ERR_TIMEOUT
+        with pytest.raises(G.NttError) as e:
+            srv.release(ids[-1])
+        assert e.value.status == 1                # NTT_ERR_ARG: still pending or running
+        for rid in ids:
+            srv.wait(rid, 600000)
+            srv.release(rid)
+    for ta, tb, tc in bufs:
+        ia, ib, ic = _to_int(ta.numpy()), _to_int(tb.numpy()), _to_int(tc.numpy())
+        assert ic % 2305843009213693951 == (ia * ib) % 2305843009213693951
