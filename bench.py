@@ -577,6 +577,9 @@ def uneven_batch(G, dev, stream, flush, med) -> dict:
         for mode, nm in [(G.NTT_BATCH_DIRECT, "direct"), (G.NTT_BATCH_STREAMS, "streams"),
                          (G.NTT_BATCH_GRAPH, "graph")]:
             modes[nm + "_ms"] = med(lambda: bp.run(a, b, c, ws, mode, stream=stream), 5, warm=2)
+        # device time by kernel in one direct-mode run (launch profiling)
+        per, _ = profile_window(G, lambda: bp.run(a, b, c, ws, G.NTT_BATCH_DIRECT, stream=stream), flush, 1)
+        by_kernel = {k: round(sum(v), 4) for k, v in sorted(per.items(), key=lambda kv: -sum(kv[1]))}
         # one call per product
         L = np.asarray(lengths, dtype=np.int64)
         logn = np.array([max(1, int(2 * v - 2).bit_length()) for v in L])   # ceil(log2(2 L - 1))
@@ -617,6 +620,7 @@ def uneven_batch(G, dev, stream, flush, med) -> dict:
                                 "Python loop over prebuilt ctypes arguments (power-of-two sizes, no TFT)",
             "batched_over_per_product": loop_ms / modes["graph_ms"],
             "best_mode_products_per_s": count / (best * 1e-3),
+            "direct_mode_kernel_ms": by_kernel,
             "per_product_equals_batched": same}
 
 

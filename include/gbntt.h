@@ -71,6 +71,9 @@ enum ntt_status {
 #define NTT_MM_MONT_PRODUCT 5u /* the kernels' general (pointwise) product: x y 2^-n rem p, scaled back */
 #define NTT_MM_ADD 6u         /* the kernels' modular sum x + y rem p (Section 2.1) */
 #define NTT_MM_SUB 7u         /* the kernels' modular difference x - y rem p */
+#define NTT_MM_MONT_FIXED_W 8u   /* n = 32: Remark 8's product from the 64-bit product x y~ (no
+                                    companion), borrow-mask tail; the row pass's twiddle product */
+#define NTT_MM_MONT_PRODUCT_W 9u /* n = 32: the row pass's pointwise product (same forms), scaled back */
 
 typedef struct ntt_plan ntt_plan;
 
@@ -403,7 +406,8 @@ int intmat_mul(const intmul_plan* plan, const uint32_t* d_A, size_t na, const ui
  * implementation (4 needs p < 2^32).  NTT_MM_SHOUP / NTT_MM_MONT_FIXED read
  * the companions d_yc (from ntt_fixed_companion); other kinds ignore it.
  * NTT_MM_MONTGOMERY converts x, y to Montgomery form, multiplies with
- * Function 13 and converts back.  NTT_MM_FMA needs p < 2^50. */
+ * Function 13 and converts back.  NTT_MM_FMA needs p < 2^50.
+ * NTT_MM_MONT_FIXED_W and NTT_MM_MONT_PRODUCT_W need word_bytes = 4. */
 int ntt_modmul_vec(uint64_t p, unsigned kind, unsigned word_bytes, const uint64_t* d_x,
                    const uint64_t* d_y, const uint64_t* d_yc, uint64_t* d_z, size_t n,
                    void* stream);

@@ -37,6 +37,8 @@ NTT_MM_MONT_FIXED = 4
 NTT_MM_MONT_PRODUCT = 5
 NTT_MM_ADD = 6
 NTT_MM_SUB = 7
+NTT_MM_MONT_FIXED_W = 8
+NTT_MM_MONT_PRODUCT_W = 9
 NTT_BATCH_DIRECT = 0
 NTT_BATCH_STREAMS = 1
 NTT_BATCH_GRAPH = 2

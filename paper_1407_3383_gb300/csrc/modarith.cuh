@@ -43,6 +43,7 @@ struct Mont32 {
     using word = uint32_t;
     using tw = Tw32;
     static constexpr int kBits = 32;
+    static constexpr bool kWide = false;   // the twiddle product reads the companion
     uint32_t p;      // odd modulus < 2^32
     uint32_t pinv;   // p^-1 rem 2^32
 
@@ -88,6 +89,51 @@ struct Mont32 {
         return sub_sel(hi, l);
     }
 };
+
+// Mont32W -- Mont32's residues and tables with two different instruction
+// forms, chosen by measurement for the kernels whose work is dominated by
+// twiddle and pointwise products (the row pass and the inverse column pass
+// of the 2^16-point products):
+//  * the product x w~ (or x y) is formed as one 32 x 32 -> 64-bit multiply;
+//    its low word times p^-1 is the Montgomery quotient q, so the twiddle
+//    product needs no companion: q = lo(x w~) p^-1 equals x phi rem 2^32
+//    because phi = w~ p^-1, and the result is bit-identical to Mont32's;
+//  * the tail h - l (+p when negative) takes the borrow mask from the high
+//    word of the 64-bit difference and adds p with one multiply-add, as the
+//    sums do, moving one instruction from the ALU pipe to the multiply-add
+//    pipe.  For h, l < p the value is h - l when h >= l and h - l + p
+//    otherwise, in [0, p) either way (a zero product gives h = l = 0).
+struct Mont32W : Mont32 {
+    static constexpr bool kWide = true;   // the twiddle product ignores the companion
+    __host__ __device__ __forceinline__ explicit Mont32W(const Mont32& m) : Mont32(m) {}
+    __device__ __forceinline__ uint32_t tail(uint32_t h, uint32_t l) const {
+        const uint64_t d = static_cast<uint64_t>(h) - l;
+        const uint32_t m = static_cast<uint32_t>(d >> 32);
+        return m * (0u - p) + static_cast<uint32_t>(d);
+    }
+    // x * w rem p for any 32-bit x; reads t.w (= w 2^32 rem p) only.
+    __device__ __forceinline__ uint32_t mulw(uint32_t x, Tw32 t) const {
+        const uint64_t xw = static_cast<uint64_t>(x) * t.w;
+        const uint32_t q = static_cast<uint32_t>(xw) * pinv;
+        return tail(static_cast<uint32_t>(xw >> 32), __umulhi(q, p));
+    }
+    // x * y * 2^-32 rem p for x, y < p.
+    __device__ __forceinline__ uint32_t mulmont(uint32_t x, uint32_t y) const {
+        const uint64_t xy = static_cast<uint64_t>(x) * y;
+        const uint32_t q = static_cast<uint32_t>(xy) * pinv;
+        return tail(static_cast<uint32_t>(xy >> 32), __umulhi(q, p));
+    }
+};
+
+// The form a kernel of the row and inverse-column passes computes with:
+// Mont32W for 32-bit words, the policy itself otherwise.
+template <class Ar> struct WideForm { using type = Ar; };
+template <> struct WideForm<Mont32> { using type = Mont32W; };
+
+template <class Ar>
+__host__ __device__ __forceinline__ typename WideForm<Ar>::type wide_form(const Ar& ar) {
+    return typename WideForm<Ar>::type(ar);
+}
 
 struct Shoup64 {
     using word = uint64_t;

@@ -147,6 +147,17 @@ __global__ void k_modmul_vec(MMArgs A, const uint64_t* __restrict__ x, const uin
                     r = ar.mulmont(ar.mulmont(x32, y32), static_cast<uint32_t>(A.r2));
                     break;
                 }
+                case NTT_MM_MONT_FIXED_W: {
+                    const Mont32W ar(Mont32{p, static_cast<uint32_t>(A.pinv)});
+                    const uint32_t wm = static_cast<uint32_t>((static_cast<uint64_t>(y32) << 32) % p);
+                    r = ar.mulw(x32, Tw32{wm, 0u});
+                    break;
+                }
+                case NTT_MM_MONT_PRODUCT_W: {
+                    const Mont32W ar(Mont32{p, static_cast<uint32_t>(A.pinv)});
+                    r = ar.mulmont(ar.mulmont(x32, y32), static_cast<uint32_t>(A.r2));
+                    break;
+                }
                 case NTT_MM_ADD: {
                     const Mont32 ar{p, static_cast<uint32_t>(A.pinv)};
                     r = ar.add(x32, y32);
@@ -303,7 +314,8 @@ int modmul_rate(uint64_t p, unsigned kind, unsigned word_bytes, int iters, doubl
 
 int launch_modmul_vec(uint64_t p, unsigned kind, unsigned word_bytes, const uint64_t* x,
                       const uint64_t* y, const uint64_t* yc, uint64_t* z, size_t n, cudaStream_t st) {
-    if (kind > NTT_MM_SUB || (word_bytes != 4 && word_bytes != 8)) return NTT_ERR_ARG;
+    if (kind > NTT_MM_MONT_PRODUCT_W || (word_bytes != 4 && word_bytes != 8)) return NTT_ERR_ARG;
+    if ((kind == NTT_MM_MONT_FIXED_W || kind == NTT_MM_MONT_PRODUCT_W) && word_bytes != 4) return NTT_ERR_ARG;
     if (p < 3 || (p & 1) == 0 || (p >> 63)) return NTT_ERR_MODULUS;
     if (word_bytes == 4 && (p >> 32)) return NTT_ERR_MODULUS;
     if (word_bytes == 8 && (p >> 62) && kind != NTT_MM_MONTGOMERY && kind != NTT_MM_BARRETT)

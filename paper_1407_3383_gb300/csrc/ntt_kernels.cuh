@@ -923,9 +923,9 @@ int launch_polymul_direct(const ntt_plan* plan, const DevPlan<Ar>& dp, const typ
             kcf<<<dim3(kDLine / kDCols, nbat, 2), kDThreads, smem_c, st>>>(dp, a, na, na, b, nb, nb, ws, 2 * N, N,
                                                                            p0, desc, tft ? beta : 16);
         prof_mark(st, tma ? (tft ? "k_col_fwd_tma_tft" : "k_col_fwd_tma") : (tft ? "k_col_fwd_d_tft" : "k_col_fwd_d"));
-        krp<<<dim3(row_blocks, nbat, 1), kDRowsPerBlock * 16, smem_r, st>>>(dp, ws, 2 * N, p0, desc);
+        krp<<<dim3(row_blocks, nbat, 1), kDRowsPerBlock * 16, smem_r, st>>>(dp, wide_form(dp.ar), ws, 2 * N, p0, desc);
         prof_mark(st, tft ? "k_row_polymul_d_tft" : "k_row_polymul_d");
-        kci<<<dim3(kDLine / kDCols, nbat, 1), kDThreads, smem_c, st>>>(dp, ws, 2 * N, c, na + nb - 1,
+        kci<<<dim3(kDLine / kDCols, nbat, 1), kDThreads, smem_c, st>>>(dp, wide_form(dp.ar), ws, 2 * N, c, na + nb - 1,
                                                                        na + nb - 1, itab, p0, desc,
                                                                        tft ? beta : 16, tft_consts<Ar>(plan));
         prof_mark(st, tft ? "k_col_inv_d_tft" : "k_col_inv_d");
@@ -986,10 +986,11 @@ int launch_sub_products(const ntt_plan* core, typename Ar::word* ws, long long c
         kcf<<<dim3(kDLine / kDCols, nb, 2), kDThreads, smem_c, st>>>(dpc, ws, kSubN, S, ws + kSubN, kSubN, S, ws,
                                                                      S, kSubN, p0, nullptr, 16);
         prof_mark(st, "k_col_fwd_d");
-        krp<<<dim3(kDLine / kDRowsPerBlock, nb, 1), kDRowsPerBlock * 16, smem_r, st>>>(dpc, ws, S, p0, nullptr);
+        krp<<<dim3(kDLine / kDRowsPerBlock, nb, 1), kDRowsPerBlock * 16, smem_r, st>>>(dpc, wide_form(dpc.ar), ws, S,
+                                                                                       p0, nullptr);
         prof_mark(st, "k_row_polymul_d");
-        kci<<<dim3(kDLine / kDCols, nb, 1), kDThreads, smem_c, st>>>(dpc, ws, S, ws, kSubN, S, itab, p0, nullptr,
-                                                                     16, TftConsts<Ar>{});
+        kci<<<dim3(kDLine / kDCols, nb, 1), kDThreads, smem_c, st>>>(dpc, wide_form(dpc.ar), ws, S, ws, kSubN, S,
+                                                                     itab, p0, nullptr, 16, TftConsts<Ar>{});
         prof_mark(st, "k_col_inv_d");
     }
     return check_launch("sub-product passes");
@@ -1087,7 +1088,7 @@ int launch_ntt_direct(const DevPlan<Ar>& dp, typename Ar::word* data, long long 
         } else {
             krow<<<gr, kDNttRowsPerBlock * 16, smem_r, st>>>(dp, data, p0);
             prof_mark(st, "k_row_ntt_inv_d");
-            k_col_inv_d<Ar><<<gc, kDThreads, smem_c, st>>>(dp, data, N, data, N, N, dp.glob_inv, p0, nullptr, 16,
+            k_col_inv_d<Ar><<<gc, kDThreads, smem_c, st>>>(dp, wide_form(dp.ar), data, N, data, N, N, dp.glob_inv, p0, nullptr, 16,
                                                            TftConsts<Ar>{});
             prof_mark(st, "k_col_inv_d");
         }
@@ -1420,7 +1421,7 @@ int launch_polymat(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename A
             k_row_ntt_d<Ar, false, kDNttRowsPerBlock>
                 <<<dim3(kDLine / kDNttRowsPerBlock, nb, 1), kDNttRowsPerBlock * 16, smem_r, st>>>(dp, Ct, p0);
             prof_mark(st, "k_row_ntt_inv_d");
-            k_col_inv_d<Ar><<<dim3(kDLine / kDCols, nb, 1), kDThreads, smem_c, st>>>(dp, Ct, NL, C, 2 * d - 1,
+            k_col_inv_d<Ar><<<dim3(kDLine / kDCols, nb, 1), kDThreads, smem_c, st>>>(dp, wide_form(dp.ar), Ct, NL, C, 2 * d - 1,
                                                                                     2 * d - 1, dp.glob_inv, p0,
                                                                                     nullptr, 16, TftConsts<Ar>{});
             prof_mark(st, "k_col_inv_d");

@@ -43,7 +43,8 @@ def _run(p, kind, wb, x, y):
 
 
 KINDS32 = [G.NTT_MM_BARRETT, G.NTT_MM_SHOUP, G.NTT_MM_MONTGOMERY, G.NTT_MM_MONT_FIXED,
-           G.NTT_MM_MONT_PRODUCT, G.NTT_MM_FMA, G.NTT_MM_ADD, G.NTT_MM_SUB]
+           G.NTT_MM_MONT_PRODUCT, G.NTT_MM_FMA, G.NTT_MM_ADD, G.NTT_MM_SUB,
+           G.NTT_MM_MONT_FIXED_W, G.NTT_MM_MONT_PRODUCT_W]
 KINDS64 = [G.NTT_MM_BARRETT, G.NTT_MM_SHOUP, G.NTT_MM_MONTGOMERY, G.NTT_MM_MONT_PRODUCT,
            G.NTT_MM_ADD, G.NTT_MM_SUB]
 
@@ -59,8 +60,17 @@ def _want(p, kind, x, y):
 @pytest.mark.parametrize("p", P32)
 @pytest.mark.parametrize("kind", KINDS32)
 def test_modmul_u32(p, kind):
-    x, y = _operands(p, 1 << 16 if kind >= G.NTT_MM_ADD else 1 << 18, p ^ kind)
+    x, y = _operands(p, 1 << 16 if kind in (G.NTT_MM_ADD, G.NTT_MM_SUB) else 1 << 18, p ^ kind)
     assert (_run(p, kind, 4, x, y) == _want(p, kind, x, y)).all()
+
+
+def test_wide_forms_refuse_64_bit_words():
+    import torch
+    x = torch.zeros(4, dtype=torch.uint64, device="cuda")
+    for kind in (G.NTT_MM_MONT_FIXED_W, G.NTT_MM_MONT_PRODUCT_W):
+        with pytest.raises(G.NttError) as e:
+            G.ntt_modmul_vec(W.P1, kind, 8, x, x, None, x)
+        assert e.value.status == 1
 
 
 @pytest.mark.parametrize("p", P64)
@@ -75,7 +85,7 @@ def test_modmul_u64(p, kind):
 @pytest.mark.parametrize("p", [17, 257, 7681])
 @pytest.mark.parametrize("kind", KINDS32)
 def test_modmul_exhaustive_small_primes(p, kind):
-    if kind >= G.NTT_MM_ADD and p > 257:
+    if kind in (G.NTT_MM_ADD, G.NTT_MM_SUB) and p > 257:
         pytest.skip("sums and differences: exhaustive on the smaller primes")
     x = np.repeat(np.arange(p, dtype=np.uint64), p)
     y = np.tile(np.arange(p, dtype=np.uint64), p)
