@@ -62,6 +62,21 @@ __device__ __forceinline__ typename Ar::tw load_tw(const Ar& ar, const typename 
     }
 }
 
+// Twiddle i of a plan table.  The 32-bit Montgomery policies read the
+// multiplicand alone from the table's 4-byte copy `w` (whole sectors per
+// warp; the pairs would bring in every companion too), other policies the
+// (multiplicand, companion) pair.
+template <class Ax>
+__device__ __forceinline__ typename Ax::tw tw_at(const Ax& ar, const typename Ax::tw* pairs, const uint32_t* w,
+                                                 long long i) {
+    if constexpr (std::is_base_of<Mont32, Ax>::value) {
+        const uint32_t x = w[i];
+        return Tw32{x, Ax::kWide ? 0u : x * ar.pinv};
+    } else {
+        return pairs[i];
+    }
+}
+
 // 16-row blocks of the column transforms that a product of `len` output
 // words needs (the TFT length rounded up to whole blocks: 1..16).
 __host__ __device__ inline int tft_blocks(long long len) {
@@ -86,7 +101,7 @@ __device__ __forceinline__ int dcol_rows(long long len, long long c) {
 // Algorithm 1's rows, its outer 16-point pass truncated to B outputs.
 template <class Ar, bool ZHALF, bool TFT = false>
 __global__ void __launch_bounds__(kDThreads, sizeof(typename Ar::word) == 4 ? kDColMinBlocks : kDColMinBlocks64)
-k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long len0, long long sstride0,
+k_col_fwd_d(DevPlan<Ar> P, const Ar ar, const typename Ar::word* __restrict__ src0, long long len0, long long sstride0,
             const typename Ar::word* __restrict__ src1, long long len1, long long sstride1,
             typename Ar::word* __restrict__ dst, long long dst_stride, long long dst_off1, long long prod_base,
             const BatchDesc* __restrict__ desc, int beta) {
@@ -113,6 +128,7 @@ k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long
     const int rows = dcol_rows(len, c0 + v);
     const word* in = src + c0 + v;
     const tw* ltab = P.line_fwd[kDLog];
+    const uint32_t* ltab_w = P.wline[0];
 #pragma unroll
     for (int i = 0; i < kDItems; ++i) {
         const int j1 = g + kDGroups * i;
@@ -124,12 +140,12 @@ k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long
             if ((!ZHALF || t < 8) && row < rows) x[t] = in[static_cast<long long>(row) * kDLine];
         }
         if (TFT)
-            tdif16<Ar, ZHALF>(P.ar, x, P.rc, B);
+            tdif16<Ar, ZHALF>(ar, x, P.rc, B);
         else
-            dif_regs<Ar, 16, ZHALF>(P.ar, x, P.rc);
+            dif_regs<Ar, 16, ZHALF>(ar, x, P.rc);
 #pragma unroll
         for (int t = 1; t < 16; ++t)
-            if (!TFT || t < B) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, ltab + j1 * 16 + t));
+            if (!TFT || t < B) x[t] = ar.mulw(x[t], tw_at(ar, ltab, ltab_w, j1 * 16 + t));
 #pragma unroll
         for (int t = 0; t < 16; ++t)
             if (!TFT || t < B) sm[(16 * t + j1) * kDCols + v] = x[t];
@@ -137,19 +153,30 @@ k_col_fwd_d(DevPlan<Ar> P, const typename Ar::word* __restrict__ src0, long long
     __syncthreads();
     word* out = dst + prod * dst_stride + (blockIdx.z ? dst_off1 : 0) + c0 + v;
     const tw* gt = P.glob_fwd + c0 + v;
+    const uint32_t* gt_w = P.wglob[0] ? P.wglob[0] + c0 + v : nullptr;
 #pragma unroll
     for (int i = 0; i < kDItems; ++i) {
         const int blk = g + kDGroups * i;
         if (TFT && blk >= B) continue;
+        // the step-2 twiddles are loaded before any store to dst: the
+        // compiler cannot prove that the plan tables and dst do not
+        // overlap, and a load after a store would wait for it (16 L2 round
+        // trips one after another instead of one)
+        tw w[16];
+        if constexpr (sizeof(word) == 4) {            // 32-bit words: before the pass, to overlap it
+#pragma unroll
+            for (int t = 0; t < 16; ++t) w[t] = tw_at(ar, gt, gt_w, (16 * blk + t) * kDLine);
+        }
         word x[16];
 #pragma unroll
         for (int t = 0; t < 16; ++t) x[t] = sm[(16 * blk + t) * kDCols + v];
-        dif_regs<Ar, 16>(P.ar, x, P.rc);
+        dif_regs<Ar, 16>(ar, x, P.rc);
+        if constexpr (sizeof(word) != 4) {            // wider words: after it (register pressure)
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            const long long pos = 16 * blk + t;
-            out[pos * kDLine] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, gt + pos * kDLine));
+            for (int t = 0; t < 16; ++t) w[t] = tw_at(ar, gt, gt_w, (16 * blk + t) * kDLine);
         }
+#pragma unroll
+        for (int t = 0; t < 16; ++t) out[(16 * blk + t) * kDLine] = ar.mulw(x[t], w[t]);
     }
 }
 
@@ -180,6 +207,7 @@ k_col_fwd_tma(DevPlan<Ar> P, const __grid_constant__ CUtensorMap map_a, const __
         return;
     const int B = TFT ? beta : 16;
     const tw* ltab = P.line_fwd[kDLog];
+    const uint32_t* ltab_w = P.wline[0];
 #pragma unroll
     for (int i = 0; i < kDItems; ++i) {
         const int j1 = g + kDGroups * i;
@@ -192,7 +220,7 @@ k_col_fwd_tma(DevPlan<Ar> P, const __grid_constant__ CUtensorMap map_a, const __
             dif_regs<Ar, 16, true>(P.ar, x, P.rc);
 #pragma unroll
         for (int t = 1; t < 16; ++t)
-            if (!TFT || t < B) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, ltab + j1 * 16 + t));
+            if (!TFT || t < B) x[t] = P.ar.mulw(x[t], tw_at(P.ar, ltab, ltab_w, j1 * 16 + t));
 #pragma unroll
         for (int t = 0; t < 16; ++t)
             if (!TFT || t < B) sm[(16 * t + j1) * kDCols + v] = x[t];
@@ -200,19 +228,20 @@ k_col_fwd_tma(DevPlan<Ar> P, const __grid_constant__ CUtensorMap map_a, const __
     __syncthreads();
     word* out = dst + prod * dst_stride + (blockIdx.z ? dst_off1 : 0) + c0 + v;
     const tw* gt = P.glob_fwd + c0 + v;
+    const uint32_t* gt_w = P.wglob[0] ? P.wglob[0] + c0 + v : nullptr;
 #pragma unroll
     for (int i = 0; i < kDItems; ++i) {
         const int blk = g + kDGroups * i;
         if (TFT && blk >= B) continue;
+        tw w[16];                                     // loaded before the stores (see k_col_fwd_d)
+#pragma unroll
+        for (int t = 0; t < 16; ++t) w[t] = tw_at(P.ar, gt, gt_w, (16 * blk + t) * kDLine);
         word x[16];
 #pragma unroll
         for (int t = 0; t < 16; ++t) x[t] = sm[(16 * blk + t) * kDCols + v];
         dif_regs<Ar, 16>(P.ar, x, P.rc);
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            const long long pos = 16 * blk + t;
-            out[pos * kDLine] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, gt + pos * kDLine));
-        }
+        for (int t = 0; t < 16; ++t) out[(16 * blk + t) * kDLine] = P.ar.mulw(x[t], w[t]);
     }
 }
 
@@ -304,6 +333,7 @@ k_row_polymul_d(DevPlan<Ar> P, const typename WideForm<Ar>::type ar, typename Ar
     const int j1 = threadIdx.x & 15, r = threadIdx.x >> 4;
     // outer forward pass of row r of operand i (line RPB i + r)
     const tw* lf = P.line256_t[0];
+    const uint32_t* lf_w = P.wline_t[0];
 #pragma unroll 1
     for (int i = 0; i < 2; ++i) {
         const word* in = base + i * N + static_cast<long long>(r0 + r) * kDLine + j1;
@@ -312,7 +342,7 @@ k_row_polymul_d(DevPlan<Ar> P, const typename WideForm<Ar>::type ar, typename Ar
         for (int t = 0; t < 16; ++t) x[t] = in[16 * t];
         dif_regs<Ax, 16>(ar, x, P.rc);
 #pragma unroll
-        for (int t = 1; t < 16; ++t) x[t] = ar.mulw(x[t], load_tw<Ax, true>(ar, lf + t * 16 + j1));
+        for (int t = 1; t < 16; ++t) x[t] = ar.mulw(x[t], tw_at(ar, lf, lf_w, t * 16 + j1));
 #pragma unroll
         for (int t = 0; t < 16; ++t) sm[RL::at(RPB * i + r, 16 * t + j1)] = x[t];
     }
@@ -336,11 +366,12 @@ k_row_polymul_d(DevPlan<Ar> P, const typename WideForm<Ar>::type ar, typename Ar
     // outer inverse pass of row r of the product
     {
         const tw* li = P.line256_t[1];
+        const uint32_t* li_w = P.wline_t[1];
         word x[16];
 #pragma unroll
         for (int t = 0; t < 16; ++t) x[t] = sm[RL::at(r, 16 * t + j1)];
 #pragma unroll
-        for (int t = 1; t < 16; ++t) x[t] = ar.mulw(x[t], load_tw<Ax, true>(ar, li + t * 16 + j1));
+        for (int t = 1; t < 16; ++t) x[t] = ar.mulw(x[t], tw_at(ar, li, li_w, t * 16 + j1));
         dit_regs<Ax, 16>(ar, x, P.rci);
         word* o = base + static_cast<long long>(r0 + r) * kDLine + j1;
 #pragma unroll
@@ -366,11 +397,12 @@ k_row_ntt_d(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long prod_
     word x[16];
     if (FWD) {
         const tw* lf = P.line256_t[0];
+        const uint32_t* lf_w = P.wline_t[0];
 #pragma unroll
         for (int t = 0; t < 16; ++t) x[t] = line[16 * t + j1];
         dif_regs<Ar, 16>(P.ar, x, P.rc);
 #pragma unroll
-        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, lf + t * 16 + j1));
+        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], tw_at(P.ar, lf, lf_w, t * 16 + j1));
 #pragma unroll
         for (int t = 0; t < 16; ++t) sm[RL::at(r, 16 * t + j1)] = x[t];
         __syncthreads();
@@ -381,6 +413,7 @@ k_row_ntt_d(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long prod_
         sm_store16(line + 16 * j1, x);
     } else {
         const tw* li = P.line256_t[1];
+        const uint32_t* li_w = P.wline_t[1];
         sm_load16(line + 16 * j1, x);
         dit_regs<Ar, 16>(P.ar, x, P.rci);
         sm_store16(sm + RL::at(r, 16 * j1), x);
@@ -388,7 +421,7 @@ k_row_ntt_d(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long prod_
 #pragma unroll
         for (int t = 0; t < 16; ++t) x[t] = sm[RL::at(r, 16 * t + j1)];
 #pragma unroll
-        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], load_tw<Ar, true>(P.ar, li + t * 16 + j1));
+        for (int t = 1; t < 16; ++t) x[t] = P.ar.mulw(x[t], tw_at(P.ar, li, li_w, t * 16 + j1));
         dit_regs<Ar, 16>(P.ar, x, P.rci);
 #pragma unroll
         for (int t = 0; t < 16; ++t) line[16 * t + j1] = x[t];
@@ -407,7 +440,8 @@ __global__ void __launch_bounds__(kDThreads, sizeof(typename Ar::word) == 4 ? kD
 k_col_inv_d(DevPlan<Ar> P, const typename WideForm<Ar>::type ar, const typename Ar::word* __restrict__ src,
             long long src_stride,
             typename Ar::word* __restrict__ dst, long long out_len, long long dst_stride,
-            const typename Ar::tw* __restrict__ itab, long long prod_base, const BatchDesc* __restrict__ desc,
+            const typename Ar::tw* __restrict__ itab, const uint32_t* __restrict__ itab_w, long long prod_base,
+            const BatchDesc* __restrict__ desc,
             int beta, TftConsts<Ar> K) {
     using word = typename Ar::word;
     using tw = typename Ar::tw;
@@ -419,6 +453,7 @@ k_col_inv_d(DevPlan<Ar> P, const typename WideForm<Ar>::type ar, const typename 
     const long long prod = prod_base + blockIdx.y;
     const word* in = src + prod * src_stride + c0 + v;
     const tw* gt = itab + c0 + v;
+    const uint32_t* gt_w = itab_w ? itab_w + c0 + v : nullptr;
     int B = 16;
     if (TFT) B = desc ? tft_blocks(static_cast<long long>(desc[prod].na) + desc[prod].nb - 1) : beta;
 #pragma unroll
@@ -429,7 +464,7 @@ k_col_inv_d(DevPlan<Ar> P, const typename WideForm<Ar>::type ar, const typename 
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
             const long long pos = 16 * blk + t;
-            x[t] = ar.mulw(in[pos * kDLine], load_tw<Ax, true>(ar, gt + pos * kDLine));
+            x[t] = ar.mulw(in[pos * kDLine], tw_at(ar, gt, gt_w, pos * kDLine));
         }
         dit_regs<Ax, 16>(ar, x, P.rci);
 #pragma unroll
@@ -447,6 +482,7 @@ k_col_inv_d(DevPlan<Ar> P, const typename WideForm<Ar>::type ar, const typename 
     const int rows = dcol_rows(out_len, c0 + v);
     word* o = outp + c0 + v;
     const tw* ltab = P.line_inv[kDLog];
+    const uint32_t* ltab_w = P.wline[1];
 #pragma unroll
     for (int i = 0; i < kDItems; ++i) {
         const int j1 = g + kDGroups * i;
@@ -455,7 +491,7 @@ k_col_inv_d(DevPlan<Ar> P, const typename WideForm<Ar>::type ar, const typename 
         for (int t = 0; t < 16; ++t) x[t] = (!TFT || t < B) ? sm[(16 * t + j1) * kDCols + v] : word(0);
 #pragma unroll
         for (int t = 1; t < 16; ++t)
-            if (!TFT || t < B) x[t] = ar.mulw(x[t], load_tw<Ax, true>(ar, ltab + j1 * 16 + t));
+            if (!TFT || t < B) x[t] = ar.mulw(x[t], tw_at(ar, ltab, ltab_w, j1 * 16 + t));
         if (TFT)
             itft16_z16(P.ar, x, P.rc, P.rci, K, B);
         else

@@ -57,6 +57,13 @@ struct DevPlan {
     const tw* glob_inv;              // w_N^-(j1 [j2]_k2) * N^-1
     const tw* plain_fwd;             // [e] = w_N^e, e < N/2
     const tw* plain_inv;
+    // 32-bit plans only (null otherwise): the multiplicands w~ alone of the
+    // tables the direct 2^16-point kernels read, 4 bytes per entry, so a warp
+    // reads whole sectors of them instead of every other word of the pairs.
+    // [0] forward, [1] inverse.
+    const uint32_t* wline[2];        // line_fwd / line_inv at logM = 8
+    const uint32_t* wline_t[2];      // line256_t
+    const uint32_t* wglob[2];        // glob_fwd, glob_inv
 };
 
 // One product of an uneven batch: word offsets of its operands and output in

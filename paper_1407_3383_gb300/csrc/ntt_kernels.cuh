@@ -920,13 +920,13 @@ int launch_polymul_direct(const ntt_plan* plan, const DevPlan<Ar>& dp, const typ
             kct<<<dim3(kDLine / kDCols, nbat, 2), kDThreads, smem_t, st>>>(dp, map_a, map_b, ws, 2 * N, N, p0,
                                                                            tft ? beta : 16, err);
         else
-            kcf<<<dim3(kDLine / kDCols, nbat, 2), kDThreads, smem_c, st>>>(dp, a, na, na, b, nb, nb, ws, 2 * N, N,
+            kcf<<<dim3(kDLine / kDCols, nbat, 2), kDThreads, smem_c, st>>>(dp, dp.ar, a, na, na, b, nb, nb, ws, 2 * N, N,
                                                                            p0, desc, tft ? beta : 16);
         prof_mark(st, tma ? (tft ? "k_col_fwd_tma_tft" : "k_col_fwd_tma") : (tft ? "k_col_fwd_d_tft" : "k_col_fwd_d"));
         krp<<<dim3(row_blocks, nbat, 1), kDRowsPerBlock * 16, smem_r, st>>>(dp, wide_form(dp.ar), ws, 2 * N, p0, desc);
         prof_mark(st, tft ? "k_row_polymul_d_tft" : "k_row_polymul_d");
         kci<<<dim3(kDLine / kDCols, nbat, 1), kDThreads, smem_c, st>>>(dp, wide_form(dp.ar), ws, 2 * N, c, na + nb - 1,
-                                                                       na + nb - 1, itab, p0, desc,
+                                                                       na + nb - 1, itab, plan->glob_inv_pm_w, p0, desc,
                                                                        tft ? beta : 16, tft_consts<Ar>(plan));
         prof_mark(st, tft ? "k_col_inv_d_tft" : "k_col_inv_d");
     }
@@ -983,14 +983,15 @@ int launch_sub_products(const ntt_plan* core, typename Ar::word* ws, long long c
     const auto* itab = static_cast<const typename Ar::tw*>(core->glob_inv_pm);
     for (long long p0 = 0; p0 < count; p0 += kMaxGridY) {
         const unsigned nb = static_cast<unsigned>(std::min(count - p0, kMaxGridY));
-        kcf<<<dim3(kDLine / kDCols, nb, 2), kDThreads, smem_c, st>>>(dpc, ws, kSubN, S, ws + kSubN, kSubN, S, ws,
+        kcf<<<dim3(kDLine / kDCols, nb, 2), kDThreads, smem_c, st>>>(dpc, dpc.ar, ws, kSubN, S, ws + kSubN, kSubN, S, ws,
                                                                      S, kSubN, p0, nullptr, 16);
         prof_mark(st, "k_col_fwd_d");
         krp<<<dim3(kDLine / kDRowsPerBlock, nb, 1), kDRowsPerBlock * 16, smem_r, st>>>(dpc, wide_form(dpc.ar), ws, S,
                                                                                        p0, nullptr);
         prof_mark(st, "k_row_polymul_d");
         kci<<<dim3(kDLine / kDCols, nb, 1), kDThreads, smem_c, st>>>(dpc, wide_form(dpc.ar), ws, S, ws, kSubN, S,
-                                                                     itab, p0, nullptr, 16, TftConsts<Ar>{});
+                                                                     itab, core->glob_inv_pm_w, p0, nullptr, 16,
+                                                                     TftConsts<Ar>{});
         prof_mark(st, "k_col_inv_d");
     }
     return check_launch("sub-product passes");
@@ -1080,7 +1081,7 @@ int launch_ntt_direct(const DevPlan<Ar>& dp, typename Ar::word* data, long long 
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
         const dim3 gc(kDLine / kDCols, nbat, 1), gr(kDLine / kDNttRowsPerBlock, nbat, 1);
         if (fwd) {
-            k_col_fwd_d<Ar, false><<<gc, kDThreads, smem_c, st>>>(dp, data, N, N, data, N, N, data, N, 0, p0,
+            k_col_fwd_d<Ar, false><<<gc, kDThreads, smem_c, st>>>(dp, dp.ar, data, N, N, data, N, N, data, N, 0, p0,
                                                                   nullptr, 16);
             prof_mark(st, "k_col_fwd_d");
             krow<<<gr, kDNttRowsPerBlock * 16, smem_r, st>>>(dp, data, p0);
@@ -1088,7 +1089,7 @@ int launch_ntt_direct(const DevPlan<Ar>& dp, typename Ar::word* data, long long 
         } else {
             krow<<<gr, kDNttRowsPerBlock * 16, smem_r, st>>>(dp, data, p0);
             prof_mark(st, "k_row_ntt_inv_d");
-            k_col_inv_d<Ar><<<gc, kDThreads, smem_c, st>>>(dp, wide_form(dp.ar), data, N, data, N, N, dp.glob_inv, p0, nullptr, 16,
+            k_col_inv_d<Ar><<<gc, kDThreads, smem_c, st>>>(dp, wide_form(dp.ar), data, N, data, N, N, dp.glob_inv, dp.wglob[1], p0, nullptr, 16,
                                                            TftConsts<Ar>{});
             prof_mark(st, "k_col_inv_d");
         }
@@ -1360,7 +1361,7 @@ int launch_polymat(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename A
             return check_launch("smem attr");
         for (long long p0 = 0; p0 < nn; p0 += kMaxGridY) {
             const unsigned nb = static_cast<unsigned>(std::min(nn - p0, kMaxGridY));
-            kcf<<<dim3(kDLine / kDCols, nb, 2), kDThreads, smem_c, st>>>(dp, A, d, d, B, d, d, ws, NL, nn * NL, p0,
+            kcf<<<dim3(kDLine / kDCols, nb, 2), kDThreads, smem_c, st>>>(dp, dp.ar, A, d, d, B, d, d, ws, NL, nn * NL, p0,
                                                                         nullptr, 16);
             prof_mark(st, "k_col_fwd_d");
         }
@@ -1422,7 +1423,7 @@ int launch_polymat(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename A
                 <<<dim3(kDLine / kDNttRowsPerBlock, nb, 1), kDNttRowsPerBlock * 16, smem_r, st>>>(dp, Ct, p0);
             prof_mark(st, "k_row_ntt_inv_d");
             k_col_inv_d<Ar><<<dim3(kDLine / kDCols, nb, 1), kDThreads, smem_c, st>>>(dp, wide_form(dp.ar), Ct, NL, C, 2 * d - 1,
-                                                                                    2 * d - 1, dp.glob_inv, p0,
+                                                                                    2 * d - 1, dp.glob_inv, dp.wglob[1], p0,
                                                                                     nullptr, 16, TftConsts<Ar>{});
             prof_mark(st, "k_col_inv_d");
         }

@@ -24,7 +24,9 @@ struct ntt_plan {
     // inverse step-2 twiddles times n^-1 R (products after Montgomery
     // pointwise steps); passed to the kernels as an argument of its own
     const void* glob_inv_pm = nullptr;
+    const uint32_t* glob_inv_pm_w = nullptr;   // its multiplicands alone (32-bit plans)
     size_t table_bytes = 0;
+    void* d_wtables = nullptr;  // 32-bit plans: the multiplicand-only tables (DevPlan::wline ...)
     gbntt::DevPlan<gbntt::Mont32> dp32{};
     gbntt::DevPlan<gbntt::Shoup64L> dp64{};
     gbntt::DevPlan<gbntt::Fma50> dpf{};         // NTT_FLAG_FP64 plans

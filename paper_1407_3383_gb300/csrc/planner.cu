@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/gbntt.h"
@@ -395,6 +396,42 @@ static int finish_plan(ntt_plan* P, DevPlan<Ar>& dp, Conv conv, uint64_t pm_fact
     P->glob_inv_pm = at(glob_off[2]);
     dp.plain_fwd = at(plain_off[0]);
     dp.plain_inv = at(plain_off[1]);
+    if constexpr (std::is_same<TwT, Tw32>::value) {
+        // multiplicand-only copies of the direct kernels' tables
+        const size_t srcs[7] = {line_off[0][kMaxLineLog], line_off[1][kMaxLineLog], linet_off[0], linet_off[1],
+                                glob_off[0], glob_off[1], glob_off[2]};
+        const size_t lens[7] = {256, 256, 256, 256, size_t(1) << P->log2n, size_t(1) << P->log2n,
+                                size_t(1) << P->log2n};
+        std::vector<uint32_t> w;
+        size_t woff[7];
+        for (int i = 0; i < 7; ++i) {
+            woff[i] = SIZE_MAX;
+            if (srcs[i] == SIZE_MAX) continue;
+            woff[i] = w.size();
+            for (size_t e = 0; e < lens[i]; ++e) w.push_back(tb.data[srcs[i] + e].w);
+            while (w.size() % 64) w.push_back(0);    // 256-byte aligned pieces
+        }
+        if (!w.empty()) {
+            if (cudaMalloc(&P->d_wtables, w.size() * 4) != cudaSuccess) {
+                cudaGetLastError();
+                gbntt_set_error("cudaMalloc of plan tables failed");
+                return NTT_ERR_OOM;
+            }
+            if (cudaMemcpy(P->d_wtables, w.data(), w.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+                gbntt_set_error(std::string("table upload: ") + cudaGetErrorString(cudaGetLastError()));
+                return NTT_ERR_CUDA;
+            }
+            const uint32_t* wb = static_cast<const uint32_t*>(P->d_wtables);
+            auto wat = [&](int i) -> const uint32_t* { return woff[i] == SIZE_MAX ? nullptr : wb + woff[i]; };
+            dp.wline[0] = wat(0);
+            dp.wline[1] = wat(1);
+            dp.wline_t[0] = wat(2);
+            dp.wline_t[1] = wat(3);
+            dp.wglob[0] = wat(4);
+            dp.wglob[1] = wat(5);
+            P->glob_inv_pm_w = wat(6);
+        }
+    }
     return NTT_OK;
 }
 
@@ -506,6 +543,7 @@ extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_p
         if (P->core) ntt_plan_destroy(P->core);
         if (P->d_pre) cudaFree(P->d_pre);
         if (P->d_tables) cudaFree(P->d_tables);
+        if (P->d_wtables) cudaFree(P->d_wtables);
         delete P;
         return rc;
     }
@@ -524,12 +562,13 @@ extern "C" int ntt_plan_destroy(ntt_plan* plan) {
         cudaFree(plan->d_pre);
         cudaSetDevice(cur);
     }
-    if (plan->d_tables) {
+    if (plan->d_tables || plan->d_wtables) {
         int cur = 0;
         cudaGetDevice(&cur);
         cudaSetDevice(plan->device);
         cudaDeviceSynchronize();
-        cudaFree(plan->d_tables);
+        if (plan->d_tables) cudaFree(plan->d_tables);
+        if (plan->d_wtables) cudaFree(plan->d_wtables);
         cudaSetDevice(cur);
     }
     delete plan;
