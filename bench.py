@@ -71,14 +71,18 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", default=None, choices=["fused"],
                     help="run only the fused timed steps (for profiler captures)")
-    ap.add_argument("--workload", default="polymul", choices=["polymul", "serve", "modmul", "suite", "fp64", "tft"],
+    ap.add_argument("--workload", default="polymul",
+                    choices=["polymul", "serve", "modmul", "suite", "fp64", "tft", "single_product",
+                             "transform_2e24_u64", "products_2e12_u64", "uneven_10000", "serving"],
                     help="polymul: the batched product (headline); serve: the Poisson "
                          "stream of integer products through the serving loop; modmul: "
                          "throughput of each reduction; suite: the other workloads and the "
                          "matrix products, one context line each; fp64: transforms over "
                          "doubles (Function 16) against the integer ones at Table 12's sizes; "
                          "tft: 2^16-point products by output length class (truncated "
-                         "transforms against the full length)")
+                         "transforms against the full length); single_product, "
+                         "transform_2e24_u64, products_2e12_u64, uneven_10000, serving: one of "
+                         "the workloads the default line carries, alone (profiler captures)")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per stream")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape (profiler captures)")
@@ -451,28 +455,48 @@ def hbm_roofline(nbytes: float, seconds: float, hbm: float) -> dict:
             "alg_bytes": nbytes}
 
 
-def run_workloads(G, dev, stream, flush, peak_gops: float, hbm: float) -> dict:
+def run_workloads(G, dev, stream, flush, peak_gops: float, hbm: float, only=None) -> dict:
     """The workloads other than the headline, each with its own config and
     rooflines: one 4096-point product (latency), one 2^24-point transform and
     1024 products of 2^12 words mod a 62-bit prime, the 10,000-product uneven
     batch against one library call per product, and a closed-loop serving
-    run.  Device time with CUDA events on the launching stream, L2 flushed
-    before each timed repetition; every result is checked (against the
-    oracle, a round trip, or another schedule)."""
-    import numpy as np
+    run (`only` selects one of them by name).  Device time with CUDA events
+    on the launching stream, L2 flushed before each timed repetition; every
+    result is checked (against the oracle, a round trip, or another
+    schedule)."""
+    import statistics as _st
     import torch
-    import oracle as O
-    from paper_1407_3383_gb300 import workloads as W
-    res = {}
 
     def med(step, reps, warm=3):
         for _ in range(warm):
             step()
         torch.cuda.synchronize()
-        return statistics.median(timed_steps(step, flush, reps, stream))
+        return _st.median(timed_steps(step, flush, reps, stream))
 
-    # -- one product of two length-2048 operands mod 998244353 (4096 points)
-    t0 = time.perf_counter()
+    parts = {
+        "single_product": lambda: wl_single_product(G, dev, stream, med, peak_gops),
+        "transform_2e24_u64": lambda: wl_transform_2e24(G, dev, stream, med, peak_gops, hbm),
+        "products_2e12_u64": lambda: wl_products_2e12(G, dev, stream, med, peak_gops, hbm),
+        "uneven_10000": lambda: uneven_batch(G, dev, stream, flush, med),
+        "serving": lambda: serve_closed_loop(G, requests=48),
+    }
+    res = {}
+    for name, fn in parts.items():
+        if only and name != only:
+            continue
+        t0 = time.perf_counter()
+        res[name] = fn()
+        res[name]["wall_s"] = time.perf_counter() - t0
+    return res
+
+
+def wl_single_product(G, dev, stream, med, peak_gops: float) -> dict:
+    """One product of two length-2048 operands mod 998244353 (4096 points):
+    latency per call with L2 flushed, and the graph-replayed rate."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_1407_3383_gb300 import workloads as W
     p, a, b = W.config0()
     with G.Plan(p, 12) as plan:
         da = torch.from_numpy(a.astype(np.uint32)).to(dev)
@@ -490,17 +514,20 @@ def run_workloads(G, dev, stream, flush, peak_gops: float, hbm: float) -> dict:
                     G.polymul_mod_p(plan, da, 2048, db, 2048, dc, stream=side)
         gms = med(lambda: graph.replay(), 10)
         ops = fused_kernel_ops(12, 2048, 2048, 1, plan.info.tile_max_log)["k_tile_polymul"]
-        res["single_product"] = {
+        return {
             "config": {"workload": "1 product 2048 x 2048 mod 998244353 (119*2^23+1), 4096-point NTTs, u32",
                        "l2": "flushed before each call"},
             "metric": "latency per product", "value": 1e3 * ms, "unit": "us", "higher_is_better": False,
             "graph_replayed_products_per_s": 100 / (gms * 1e-3),
             "roofline": dict(alu_roofline(ops, ms * 1e-3, peak_gops), bound="latency",
                              note="one thread block on one of 152 SMs"),
-            "matches_oracle": ok, "wall_s": time.perf_counter() - t0}
+            "matches_oracle": ok}
 
-    # -- one 2^24-point transform mod P1, forward then inverse
-    t0 = time.perf_counter()
+
+def wl_transform_2e24(G, dev, stream, med, peak_gops: float, hbm: float) -> dict:
+    """One 2^24-point transform mod P1, forward then inverse."""
+    import torch
+    from paper_1407_3383_gb300 import workloads as W
     p, x = W.config2_transform()
     with G.Plan(p, 24) as plan:
         dx = torch.from_numpy(x).to(dev)
@@ -511,17 +538,20 @@ def run_workloads(G, dev, stream, flush, peak_gops: float, hbm: float) -> dict:
         ops = 2 * ntt64_ops(n)
         nbytes = 2 * 2 * n * 8                              # each transform reads and writes n words once
         sec = (fms + ims) * 1e-3
-        res["transform_2e24_u64"] = {
+        return {
             "config": {"workload": "one 2^24-point transform mod P1 = 2097222*2^40+1 (62-bit), forward then "
                                    "inverse, u64", "l2": "flushed before each transform"},
             "metric": "forward + inverse time", "value": fms + ims, "unit": "ms", "higher_is_better": False,
             "forward_ms": fms, "inverse_ms": ims,
             "roofline": alu_roofline(ops, sec, peak_gops), "hbm": hbm_roofline(nbytes, sec, hbm),
-            "round_trip_exact": ok, "wall_s": time.perf_counter() - t0}
-        del dx
+            "round_trip_exact": ok}
 
-    # -- 1024 products of length 2^12 mod P1 (2^13 points, u64)
-    t0 = time.perf_counter()
+
+def wl_products_2e12(G, dev, stream, med, peak_gops: float, hbm: float) -> dict:
+    """1024 products of length 2^12 mod P1 (2^13 points, u64)."""
+    import torch
+    import oracle as O
+    from paper_1407_3383_gb300 import workloads as W
     p, a, b = W.config2_products()
     with G.Plan(p, 13) as plan:
         da = torch.from_numpy(a.reshape(-1)).to(dev)
@@ -533,25 +563,13 @@ def run_workloads(G, dev, stream, flush, peak_gops: float, hbm: float) -> dict:
         ok = bool((dc.view(1024, 8191).cpu().numpy()[sel] == want).all())
         ops = polymul64_ops(13, 4096, 4096, 1024)
         nbytes = 1024 * (2 * 4096 + 8191) * 8
-        res["products_2e12_u64"] = {
+        return {
             "config": {"workload": "1024 products 2^12 x 2^12 mod P1 (62-bit), 2^13-point NTTs, u64",
                        "l2": "flushed before each call"},
             "metric": "products/s", "value": 1024 / (ms * 1e-3), "unit": "products/s", "higher_is_better": True,
             "ms": ms, "roofline": alu_roofline(ops, ms * 1e-3, peak_gops),
             "hbm": hbm_roofline(nbytes, ms * 1e-3, hbm),
-            "oracle_checked_products": len(sel), "matches_oracle": ok, "wall_s": time.perf_counter() - t0}
-        del da, db, dc
-
-    # -- 10,000 uneven products mod P1..P3, against one library call per product
-    t0 = time.perf_counter()
-    res["uneven_10000"] = uneven_batch(G, dev, stream, flush, med)
-    res["uneven_10000"]["wall_s"] = time.perf_counter() - t0
-
-    # -- serving: closed-loop stream of integer products
-    t0 = time.perf_counter()
-    res["serving"] = serve_closed_loop(G, requests=48)
-    res["serving"]["wall_s"] = time.perf_counter() - t0
-    return res
+            "oracle_checked_products": len(sel), "matches_oracle": ok}
 
 
 def uneven_batch(G, dev, stream, flush, med) -> dict:
@@ -665,6 +683,21 @@ def serve_closed_loop(G, requests: int = 48) -> dict:
             "higher_is_better": True, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "peak_inflight": stats["peak_inflight"],
             "checked_smallest_request": ok}
+
+
+def run_one_workload(args, world, rank, local):
+    """One of the default line's other workloads, alone, as a JSON line."""
+    import torch
+    import paper_1407_3383_gb300 as G
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    probe = measure_probes(G, stream)
+    peak = probe.get("mixed_gops") or SM_COUNT * INT_LANES_PER_SM * SM_MAX_MHZ * 1e-3
+    res = run_workloads(G, dev, stream, lambda: flush_buf.fill_(1), peak, measured_hbm_gbs(), only=args.workload)
+    if rank == 0:
+        print(json.dumps(dict(res[args.workload], name=args.workload, n_gpus=world, int_probe=probe)), flush=True)
 
 
 def run_native(args, world, rank, local):
@@ -1155,6 +1188,9 @@ def main():
         run_fp64(args, world, rank, local)
     elif args.workload == "tft" and args.impl == "native":
         run_tft(args, world, rank, local)
+    elif args.workload in ("single_product", "transform_2e24_u64", "products_2e12_u64", "uneven_10000",
+                           "serving") and args.impl == "native":
+        run_one_workload(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)
     else:

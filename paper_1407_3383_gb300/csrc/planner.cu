@@ -398,8 +398,12 @@ static int finish_plan(ntt_plan* P, DevPlan<Ar>& dp, Conv conv, uint64_t pm_fact
     dp.plain_inv = at(plain_off[1]);
     if constexpr (std::is_same<TwT, Tw32>::value) {
         // multiplicand-only copies of the direct kernels' tables
+        // (the step-2 tables only at n = 2^16: larger sizes run the direct
+        // kernels of their 2^16-point child plan)
+        const bool g16 = P->log2n == 16;
         const size_t srcs[7] = {line_off[0][kMaxLineLog], line_off[1][kMaxLineLog], linet_off[0], linet_off[1],
-                                glob_off[0], glob_off[1], glob_off[2]};
+                                g16 ? glob_off[0] : SIZE_MAX, g16 ? glob_off[1] : SIZE_MAX,
+                                g16 ? glob_off[2] : SIZE_MAX};
         const size_t lens[7] = {256, 256, 256, 256, size_t(1) << P->log2n, size_t(1) << P->log2n,
                                 size_t(1) << P->log2n};
         std::vector<uint32_t> w;
