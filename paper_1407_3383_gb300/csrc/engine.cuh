@@ -64,6 +64,9 @@ struct DevPlan {
     const uint32_t* wline[2];        // line_fwd / line_inv at logM = 8
     const uint32_t* wline_t[2];      // line256_t
     const uint32_t* wglob[2];        // glob_fwd, glob_inv
+    // 64-point sub-transforms split 8 x 8 (the cluster kernel of 4096-point
+    // products): [j1*8 + t] = w_64^(+-j1 [t]_3)
+    const tw* line64x8[2];
 };
 
 // One product of an uneven batch: word offsets of its operands and output in

@@ -25,6 +25,7 @@
 #include <string>
 
 #include "../../include/gbntt.h"
+#include "cluster.cuh"
 #include "direct.cuh"
 #include "subvec.cuh"
 #include "kernels.h"
@@ -1143,6 +1144,22 @@ int launch_ntt_sub(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::wor
     return launch_ntt_direct<Ar>(dpc, data, batch * M, true, st);
 }
 
+// A few 4096-point products, each on one thread-block cluster of 8 CTAs
+// (latency: the three transforms of a product spread over 8 SMs).
+template <class Ar>
+int launch_polymul_cluster(const DevPlan<Ar>& dp, const typename Ar::word* a, long long na,
+                           const typename Ar::word* b, long long nb, long long batch, typename Ar::word* c,
+                           typename Ar::tw scale, cudaStream_t st) {
+    const bool zh = na <= 2048 && nb <= 2048;
+    auto k = zh ? k_cluster_polymul<Ar, true> : k_cluster_polymul<Ar, false>;
+    const size_t smem = cluster_smem_words() * sizeof(typename Ar::word);
+    if (allow_smem(k, smem) != cudaSuccess) return check_launch("smem attr");
+    k<<<static_cast<unsigned>(kClCtas * batch), kClThreads, smem, st>>>(dp, wide_form(dp.ar), a, na, b, nb, c,
+                                                                        scale);
+    prof_mark(st, "k_cluster_polymul");
+    return check_launch("k_cluster_polymul");
+}
+
 template <class Ar>
 int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
                          long long na, const typename Ar::word* b, long long nb, long long batch,
@@ -1152,6 +1169,10 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
     const int k = static_cast<int>(plan->log2n);
     const LaunchCfg cfg = launch_cfg(sizeof(word), k, plan->tile_max_log);
     prof_begin_call(st);
+    if constexpr (!std::is_same<Ar, Fma50>::value) {
+        if (k == kClLog && batch <= kClMaxBatch && dp.line64x8[0] && dp.tile_fwd[kClLog])
+            return launch_polymul_cluster<Ar>(dp, a, na, b, nb, batch, c, scale, st);
+    }
     if (k <= plan->tile_max_log) {
         const int lppc = cfg.lppc;
         const size_t smem = layout_words(tile_layout(k, lppc + 1)) * sizeof(word);

@@ -255,7 +255,7 @@ template <class TwT, class Conv>
 static void build_tables(ntt_plan* P, TableBuilder<TwT>& tb, Conv conv,
                          size_t (&line_off)[2][kMaxLineLog + 1], size_t (&tile_off)[2][17],
                          size_t (&glob_off)[3], size_t (&plain_off)[2], size_t (&linet_off)[2],
-                         uint64_t pm_factor) {
+                         size_t (&l64x8_off)[2], uint64_t pm_factor) {
     const uint64_t p = P->p;
     const uint64_t g = P->g;
     auto root = [&](int logm, bool fwd) {
@@ -269,6 +269,16 @@ static void build_tables(ntt_plan* P, TableBuilder<TwT>& tb, Conv conv,
         for (int lt = 0; lt <= 16; ++lt) tile_off[d][lt] = SIZE_MAX;
         plain_off[d] = SIZE_MAX;
         linet_off[d] = SIZE_MAX;
+        l64x8_off[d] = SIZE_MAX;
+        // 64-point sub-transforms split 8 x 8: [j1*8 + t] = w_64^(j1 [t]_3)
+        if (P->v2 >= 6) {
+            const uint64_t w64 = root(6, fwd);
+            const size_t off = tb.add(64);
+            for (int j1 = 0; j1 < 8; ++j1)
+                for (int t = 0; t < 8; ++t)
+                    tb.data[off + j1 * 8 + t] = conv(pow_mod(w64, uint64_t(j1) * bit_mirror(t, 3), p));
+            l64x8_off[d] = off;
+        }
         if (fwd) glob_off[0] = glob_off[1] = glob_off[2] = SIZE_MAX;
         // radix-16 pass tables for sub-transform sizes 2^5 .. 2^8
         for (int lm = 5; lm <= kMaxLineLog && lm <= static_cast<int>(P->v2); ++lm) {
@@ -360,8 +370,8 @@ static void build_tft(const ntt_plan* P, TftConsts<Ar>& K, Conv conv) {
 template <class Ar, class TwT, class Conv>
 static int finish_plan(ntt_plan* P, DevPlan<Ar>& dp, Conv conv, uint64_t pm_factor) {
     TableBuilder<TwT> tb;
-    size_t line_off[2][kMaxLineLog + 1], tile_off[2][17], glob_off[3], plain_off[2], linet_off[2];
-    build_tables<TwT>(P, tb, conv, line_off, tile_off, glob_off, plain_off, linet_off, pm_factor);
+    size_t line_off[2][kMaxLineLog + 1], tile_off[2][17], glob_off[3], plain_off[2], linet_off[2], l64x8_off[2];
+    build_tables<TwT>(P, tb, conv, line_off, tile_off, glob_off, plain_off, linet_off, l64x8_off, pm_factor);
     const uint64_t w16 = pow_mod(P->g, (P->p - 1) >> 4, P->p);
     const uint64_t w16i = pow_mod(w16, P->p - 2, P->p);
     for (int e = 0; e < 8; ++e) {
@@ -396,6 +406,8 @@ static int finish_plan(ntt_plan* P, DevPlan<Ar>& dp, Conv conv, uint64_t pm_fact
     P->glob_inv_pm = at(glob_off[2]);
     dp.plain_fwd = at(plain_off[0]);
     dp.plain_inv = at(plain_off[1]);
+    dp.line64x8[0] = at(l64x8_off[0]);
+    dp.line64x8[1] = at(l64x8_off[1]);
     if constexpr (std::is_same<TwT, Tw32>::value) {
         // multiplicand-only copies of the direct kernels' tables
         // (the step-2 tables only at n = 2^16: larger sizes run the direct

@@ -338,3 +338,22 @@ def test_polymul_host_buffers_edge_cases():
         G.polymul_mod_p_batch_host(plan, ha, 1500, hb, 1000, 5, hc, 2, stage)
         torch.cuda.synchronize()
         assert (hc.numpy().astype(np.uint64).reshape(5, 2499) == want).all()
+
+
+@pytest.mark.parametrize("p", [W.P_A, W.P_B, W.P1])
+@pytest.mark.parametrize("na,nb", [(2048, 2048), (3000, 1096), (1, 4095), (2047, 1), (1500, 700)])
+def test_cluster_products_match_oracle_and_one_block(p, na, nb):
+    """n = 4096: batches of at most 16 products run one product per
+    thread-block cluster (8 CTAs exchanging rows and columns through
+    distributed shared memory), larger batches the one-block kernel; both
+    give the oracle's product, bit for bit, zero-half and ragged lengths."""
+    g = W.SplitMix64(p ^ na ^ (nb << 20))
+    a = g.uniform_mod(p, 17 * na).reshape(17, na)
+    b = g.uniform_mod(p, 17 * nb).reshape(17, nb)
+    one_block = _polymul(p, 12, a, b)                  # 17 products: the one-block kernel
+    cluster = _polymul(p, 12, a[:16], b[:16])          # 16 products: one cluster each
+    single = _polymul(p, 12, a[5:6], b[5:6])
+    assert (cluster == one_block[:16]).all()
+    assert (single[0] == one_block[5]).all()
+    for t in (0, 7, 15):
+        assert (cluster[t] == O.polymul(p, a[t], b[t])).all()
