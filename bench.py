@@ -1177,6 +1177,36 @@ def run_tft(args, world, rank, local):
         if rank == 0:
             print(json.dumps({"metric": "2^16-point products by output length (truncated transforms)",
                               "p": p, "batch": batch, "n_gpus": world, "rows": rows}), flush=True)
+    # one-block sizes and the two-pass sizes below 2^16: 2^23 output words
+    # per call; the output needs kb of the 16 blocks of n/16 positions, and
+    # kb = 16 is what padding to n costs at every kb
+    for p, dt in [(W.P_B, np.uint32), (W.P1, np.uint64)]:
+        for log2n in range(8, 16):
+            n = 1 << log2n
+            batch = max(16, (1 << 23) >> log2n)
+            rows = []
+            with G.Plan(p, log2n) as plan:
+                ws = G.alloc_workspace(plan, batch)
+                for kb in [16, 14, 12, 10, 9]:
+                    L = kb * n // 16
+                    na = (L + 1) // 2
+                    nb = L + 1 - na
+                    a = torch.from_numpy(g.uniform_mod(p, batch * na).astype(dt)).to(dev)
+                    b = torch.from_numpy(g.uniform_mod(p, batch * nb).astype(dt)).to(dev)
+                    c = torch.empty(batch * L, dtype=a.dtype, device=dev)
+                    step = lambda: G.polymul_mod_p_batch(plan, a, na, b, nb, batch, c, G.NTT_SCHED_FUSED,
+                                                         ws, stream=stream)
+                    for _ in range(3):
+                        step()
+                    torch.cuda.synchronize()
+                    ms = statistics.median(timed_steps(step, lambda: flush_buf.fill_(1), 20, stream))
+                    rows.append({"blocks": kb, "na": na, "nb": nb, "ms": round(ms, 5)})
+                    del a, b, c
+            for r in rows:
+                r["time_vs_padded"] = round(r["ms"] / rows[0]["ms"], 3)
+            if rank == 0:
+                print(json.dumps({"metric": "products by output length (truncated transforms)", "p": p,
+                                  "log2n": log2n, "batch": batch, "rows": rows}), flush=True)
 
 
 def main():

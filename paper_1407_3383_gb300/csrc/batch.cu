@@ -6,7 +6,8 @@
 //  - products whose transform length 2^k fits one thread block
 //    (k <= tile_max_log) become items of up to 16 equal-size, equal-modulus
 //    products, ordered by decreasing size; one persistent kernel drains them
-//    from a ticket counter;
+//    from a ticket counter; each item's transforms are truncated to the
+//    blocks its longest output needs (Section 5.1's TFT);
 //  - longer products are grouped into buckets of equal (modulus, k), each
 //    run as the three global passes of the fused schedule.
 // The work of a run can be captured once into a CUDA graph whose branches
@@ -37,6 +38,7 @@ struct Bucket {
     ntt_plan* plan;
     size_t ws_off;
     long long subs;      // 2^16-point row slots kept (products of 2^17 .. 2^24 points)
+    bool tft;            // n < 2^16: every product's output needs few enough column blocks to truncate
 };
 
 }  // namespace
@@ -54,6 +56,7 @@ struct polymul_batch_plan {
     BatchDesc* d_desc = nullptr;
     void* d_items = nullptr;
     void* d_plans = nullptr;
+    void* d_tfts = nullptr;                      // inverse-TFT constants per modulus
     unsigned nitems = 0;
     size_t small_smem = 0;
     int small_grid = 0;
@@ -84,17 +87,22 @@ template <class Ar, class TwOf>
 int build_device_block(polymul_batch_plan* B, const std::vector<BatchDesc>& descs,
                        const std::vector<SmallItem<Ar>>& items, TwOf) {
     std::vector<DevPlan<Ar>> dps(B->primes.size());
+    std::vector<TftConsts<Ar>> tfts(B->primes.size());
     for (size_t i = 0; i < B->primes.size(); ++i) {
         if (!B->small_plans[i]) continue;
-        if constexpr (sizeof(typename Ar::word) == 4)
+        if constexpr (sizeof(typename Ar::word) == 4) {
             dps[i] = B->small_plans[i]->dp32;
-        else
+            tfts[i] = B->small_plans[i]->tft32;
+        } else {
             dps[i] = B->small_plans[i]->dp64;
+            tfts[i] = B->small_plans[i]->tft64;
+        }
     }
     const size_t off_desc = 0;
     const size_t off_items = align256(off_desc + descs.size() * sizeof(BatchDesc));
     const size_t off_plans = align256(off_items + items.size() * sizeof(SmallItem<Ar>));
-    const size_t total = align256(off_plans + dps.size() * sizeof(DevPlan<Ar>));
+    const size_t off_tfts = align256(off_plans + dps.size() * sizeof(DevPlan<Ar>));
+    const size_t total = align256(off_tfts + tfts.size() * sizeof(TftConsts<Ar>));
     if (cudaMalloc(&B->d_block, std::max<size_t>(total, 256)) != cudaSuccess) {
         cudaGetLastError();
         return NTT_ERR_OOM;
@@ -107,6 +115,8 @@ int build_device_block(polymul_batch_plan* B, const std::vector<BatchDesc>& desc
               reinterpret_cast<const unsigned char*>(items.data() + items.size()), host.begin() + off_items);
     std::copy(reinterpret_cast<const unsigned char*>(dps.data()),
               reinterpret_cast<const unsigned char*>(dps.data() + dps.size()), host.begin() + off_plans);
+    std::copy(reinterpret_cast<const unsigned char*>(tfts.data()),
+              reinterpret_cast<const unsigned char*>(tfts.data() + tfts.size()), host.begin() + off_tfts);
     if (total && cudaMemcpy(base, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
         gbntt_set_error("batch plan upload failed");
         return NTT_ERR_CUDA;
@@ -114,6 +124,7 @@ int build_device_block(polymul_batch_plan* B, const std::vector<BatchDesc>& desc
     B->d_desc = reinterpret_cast<BatchDesc*>(base + off_desc);
     B->d_items = base + off_items;
     B->d_plans = base + off_plans;
+    B->d_tfts = base + off_tfts;
     B->nitems = static_cast<unsigned>(items.size());
     size_t smem = 0;
     for (const auto& it : items)
@@ -131,6 +142,7 @@ int plan_products(polymul_batch_plan* B, const polymul_desc* h, size_t count, Tw
     struct Ent {
         size_t idx;
         int k;
+        bool tft;   // two-pass sizes below 2^16: truncated transforms pay for this product
     };
     std::vector<Ent> small, big;
     for (size_t t = 0; t < count; ++t) {
@@ -145,12 +157,18 @@ int plan_products(polymul_batch_plan* B, const polymul_desc* h, size_t count, Tw
             gbntt_set_error("batch descriptor " + std::to_string(t) + ": product too long for its modulus");
             return NTT_ERR_SIZE;
         }
-        (k <= tile_max ? small : big).push_back({t, k});
+        const long long nc = static_cast<long long>(d.na) + d.nb - 1;
+        const bool tft = k < 16 && tft_kb(nc, k) <= kColTftMaxBlocks;
+        (k <= tile_max ? small : big).push_back({t, k, tft});
     }
-    // items: decreasing size, then modulus
+    // items: decreasing size, then modulus, then decreasing output length
+    // (so that the products of one item need about as many blocks of the
+    // truncated transform)
+    auto out_len = [&](const Ent& e) { return static_cast<long long>(h[e.idx].na) + h[e.idx].nb - 1; };
     std::stable_sort(small.begin(), small.end(), [&](const Ent& x, const Ent& y) {
         if (x.k != y.k) return x.k > y.k;
-        return h[x.idx].prime < h[y.idx].prime;
+        if (h[x.idx].prime != h[y.idx].prime) return h[x.idx].prime < h[y.idx].prime;
+        return out_len(x) > out_len(y);
     });
     std::vector<BatchDesc> descs;
     std::vector<SmallItem<Ar>> items;
@@ -168,6 +186,8 @@ int plan_products(polymul_batch_plan* B, const polymul_desc* h, size_t count, Tw
         const uint64_t r = (B->wb == 4) ? ((1ull << 32) % p)
                                         : static_cast<uint64_t>((static_cast<unsigned __int128>(1) << 64) % p);
         it.scale = tw_of(host::mul_mod(ninv, r, p), p);
+        it.kb = k >= kTileTftMinLog ? static_cast<unsigned>(tft_kb(out_len(small[s]), k)) : 16u;
+        if (it.kb > static_cast<unsigned>(kTileTftMaxBlocks)) it.kb = 16;   // the full transforms
         while (s < small.size() && small[s].k == k && h[small[s].idx].prime == pr && it.count < cap) {
             const polymul_desc& d = h[small[s].idx];
             descs.push_back(BatchDesc{d.a_off, d.b_off, d.c_off, d.na, d.nb});
@@ -182,10 +202,11 @@ int plan_products(polymul_batch_plan* B, const polymul_desc* h, size_t count, Tw
         int rc = ntt_plan_create(B->primes[i], static_cast<unsigned>(max_small_k[i]), 0, &B->small_plans[i]);
         if (rc != NTT_OK) return rc;
     }
-    // buckets: equal (modulus, k)
+    // buckets: equal (modulus, k), and below 2^16 points equal truncation class
     std::stable_sort(big.begin(), big.end(), [&](const Ent& x, const Ent& y) {
         if (x.k != y.k) return x.k > y.k;
-        return h[x.idx].prime < h[y.idx].prime;
+        if (h[x.idx].prime != h[y.idx].prime) return h[x.idx].prime < h[y.idx].prime;
+        return x.tft < y.tft;
     });
     size_t ws = 256;   // the ticket counter
     B->ticket_off = 0;
@@ -194,12 +215,14 @@ int plan_products(polymul_batch_plan* B, const polymul_desc* h, size_t count, Tw
         bk.prime = h[big[s].idx].prime;
         bk.log2n = big[s].k;
         bk.first = static_cast<unsigned>(descs.size());
+        bk.tft = big[s].tft;
         // products of 2^17 .. 2^24 points keep lam = ceil(L / 2^16) of their
         // n2 = 2^(k-16) rows (whole blocks of n2/16 rows past 16 rows): the
         // truncated transform of Section 5.1 with Algorithm 1's rows; their
         // kept rows take consecutive slots of the bucket's workspace
         const long long n2 = bk.log2n > 16 ? (1LL << (bk.log2n - 16)) : 0;
-        while (s < big.size() && big[s].k == bk.log2n && h[big[s].idx].prime == bk.prime) {
+        while (s < big.size() && big[s].k == bk.log2n && h[big[s].idx].prime == bk.prime &&
+               big[s].tft == bk.tft) {
             const polymul_desc& d = h[big[s].idx];
             BatchDesc bd{d.a_off, d.b_off, d.c_off, d.na, d.nb, static_cast<unsigned long long>(bk.subs)};
             if (n2) {
@@ -255,7 +278,8 @@ int enqueue(polymul_batch_plan* B, const void* a, const void* b, void* c, void* 
     int rc = NTT_OK;
     if (B->nitems) {
         cudaMemsetAsync(ticket, 0, sizeof(unsigned), st0);
-        rc = launch_batch_small<Ar>(static_cast<const DevPlan<Ar>*>(B->d_plans), B->d_desc, B->d_items,
+        rc = launch_batch_small<Ar>(static_cast<const DevPlan<Ar>*>(B->d_plans),
+                                    static_cast<const TftConsts<Ar>*>(B->d_tfts), B->d_desc, B->d_items,
                                     B->nitems, ticket, A, Bp, C, B->small_smem, B->small_grid, st0);
         if (rc != NTT_OK) return rc;
     }
@@ -266,10 +290,10 @@ int enqueue(polymul_batch_plan* B, const void* a, const void* b, void* c, void* 
         word* wsp = reinterpret_cast<word*>(wsb + bk.ws_off);
         if constexpr (sizeof(word) == 4)
             rc = launch_batch_bucket<Ar>(np, np->dp32, A, Bp, C, B->d_desc + bk.first, bk.count, wsp,
-                                         np->pm_scale32, s, bk.subs);
+                                         np->pm_scale32, s, bk.subs, bk.tft);
         else
             rc = launch_batch_bucket<Ar>(np, np->dp64, A, Bp, C, B->d_desc + bk.first, bk.count, wsp,
-                                         np->pm_scale64, s, bk.subs);
+                                         np->pm_scale64, s, bk.subs, bk.tft);
         if (rc != NTT_OK) return rc;
     }
     if (spread) {

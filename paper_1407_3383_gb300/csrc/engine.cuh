@@ -81,16 +81,25 @@ struct BatchDesc {
 
 // A work item of the persistent kernel: `count` products (descriptors
 // desc[first .. first+count)) of one-block size 2^logL with modulus `prime`
-// (index into the plan array), final scaling `scale`.
+// (index into the plan array), final scaling `scale`; kb < 16: the
+// transforms are truncated to kb of the 16 blocks of 2^logL/16 positions
+// (the most that any of the item's products needs).
 template <class Ar>
 struct SmallItem {
-    unsigned first, count, prime, logL;
+    unsigned first, count, prime, logL, kb;
     typename Ar::tw scale;
 };
 
 constexpr int kSmallMaxPerItem = 16;
 
-__host__ __device__ inline int small_lppc(int logL) { return logL <= kMaxLineLog ? 4 : 0; }
+// log2 of the products per block of the one-block sizes: 16 one-line vectors
+// up to 256 words; tiles of 2^9, 2^10, 2^11 words hold 8, 4, 2 products, so
+// that a block's column phase runs at least 512 lines (measured on 2^23
+// output words per call: 2^9 points 0.26 -> 0.14 ms with 32-bit words,
+// 0.71 -> 0.30 ms with 64-bit words; 2^10: 0.21 -> 0.16, 0.49 -> 0.34 ms)
+__host__ __device__ inline int small_lppc(int logL) {
+    return logL <= kMaxLineLog ? 4 : (logL < 12 ? 12 - logL : 0);
+}
 
 // Twiddle applied to every element of a vector at the outer end of a phase:
 // element at position `pos` of line `x` of vector `v` is multiplied by
@@ -168,16 +177,18 @@ struct PhaseGeom {
 // One pass of radix R over every line: sub-transforms of size 2^logM.
 // FWD: DIF then twiddle; inverse: twiddle then DIT.  When M == R this is the
 // innermost level; the hook (if any) applies there.
+// nblk (nonzero): only the first nblk sub-transforms of every line run (the
+// kept blocks of a truncated transform).
 template <class Ar, int R, bool FWD, bool ZHALF = false>
 __device__ __forceinline__ void run_pass(const DevPlan<Ar>& P, typename Ar::word* s,
                                          const PhaseGeom& g, int logM,
-                                         const Hook<Ar>* hook) {
+                                         const Hook<Ar>* hook, int nblk = 0) {
     using word = typename Ar::word;
     using tw = typename Ar::tw;
     constexpr int lr = RadixLog<R>::v;
     const int logMR = logM - lr;                 // log of j1 range
     const int lognl = g.lognvec + g.logX;         // log of number of lines
-    const int items = 1 << (lognl + g.logL - lr);
+    const int items = nblk ? ((nblk << logMR) << lognl) : 1 << (lognl + g.logL - lr);
     const tw* ltab = (logMR > 0) ? (FWD ? P.line_fwd[logM] : P.line_inv[logM]) : nullptr;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int line = it & ((1 << lognl) - 1);
@@ -230,12 +241,12 @@ __device__ __forceinline__ void run_pass(const DevPlan<Ar>& P, typename Ar::word
 template <class Ar, bool FWD>
 __device__ __forceinline__ void run_pass_r(const DevPlan<Ar>& P, typename Ar::word* s,
                                            const PhaseGeom& g, int logM, int lr,
-                                           const Hook<Ar>* hook) {
+                                           const Hook<Ar>* hook, int nblk = 0) {
     switch (lr) {
-        case 4: run_pass<Ar, 16, FWD>(P, s, g, logM, hook); break;
-        case 3: run_pass<Ar, 8, FWD>(P, s, g, logM, hook); break;
-        case 2: run_pass<Ar, 4, FWD>(P, s, g, logM, hook); break;
-        default: run_pass<Ar, 2, FWD>(P, s, g, logM, hook); break;
+        case 4: run_pass<Ar, 16, FWD>(P, s, g, logM, hook, nblk); break;
+        case 3: run_pass<Ar, 8, FWD>(P, s, g, logM, hook, nblk); break;
+        case 2: run_pass<Ar, 4, FWD>(P, s, g, logM, hook, nblk); break;
+        default: run_pass<Ar, 2, FWD>(P, s, g, logM, hook, nblk); break;
     }
 }
 

@@ -5,6 +5,7 @@
 #include <cstddef>
 
 #include "engine.cuh"
+#include "tft.cuh"
 
 struct ntt_plan;
 
@@ -23,8 +24,8 @@ int launch_polymul_plain(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
                          cudaStream_t st);
 
 template <class Ar>
-int launch_batch_small(const DevPlan<Ar>* d_plans, const BatchDesc* d_desc, const void* d_items,
-                       unsigned nitems, unsigned* d_ticket, const typename Ar::word* a,
+int launch_batch_small(const DevPlan<Ar>* d_plans, const TftConsts<Ar>* d_tfts, const BatchDesc* d_desc,
+                       const void* d_items, unsigned nitems, unsigned* d_ticket, const typename Ar::word* a,
                        const typename Ar::word* b, typename Ar::word* c, size_t smem, int grid,
                        cudaStream_t st);
 
@@ -35,7 +36,7 @@ template <class Ar>
 int launch_batch_bucket(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
                         const typename Ar::word* b, typename Ar::word* c, const BatchDesc* d_desc,
                         long long count, typename Ar::word* ws, typename Ar::tw scale,
-                        cudaStream_t st, long long subs);
+                        cudaStream_t st, long long subs, bool tft);
 
 template <class Ar>
 int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* data, long long batch,

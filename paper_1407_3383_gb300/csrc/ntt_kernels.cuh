@@ -101,13 +101,15 @@ __host__ __device__ inline long long slab_words(const VecLayout& L) {
 // threads: tiles that leave room for one block per SM run 512 threads, so
 // that an SM holds 16 warps instead of 8; grids smaller than the GPU (a few
 // products, where each block has an SM to itself) run 1024 threads with
-// 32-bit words and 512 with 64-bit words.
-template <class Ar, int NT = kThreads>
+// 32-bit words and 512 with 64-bit words.  TFT: the transforms are
+// truncated to the kb of 16 blocks of 2^logL/16 positions that the
+// na + nb - 1 output words need (Section 5.1; logL >= 5).
+template <class Ar, int NT = kThreads, bool TFT = false>
 __global__ void __launch_bounds__(NT)
 k_tile_polymul(DevPlan<Ar> P, const typename Ar::word* __restrict__ a, long long na,
                const typename Ar::word* __restrict__ b, long long nb,
                typename Ar::word* __restrict__ c, long long batch, int logL, int lppc,
-               typename Ar::tw scale) {
+               typename Ar::tw scale, int kb, TftConsts<Ar> K) {
     using word = typename Ar::word;
     extern __shared__ __align__(16) unsigned char smraw[];
     word* sm = reinterpret_cast<word*>(smraw);
@@ -128,16 +130,24 @@ k_tile_polymul(DevPlan<Ar> P, const typename Ar::word* __restrict__ a, long long
         sm[vec_addr(LA, v + ppc, static_cast<int>(i))] = xb;
     }
     __syncthreads();
-    vec_fwd<Ar>(P, sm, LA, nullptr);
+    if (TFT)
+        vec_fwd_t<Ar>(P, sm, LA, kb, K);
+    else
+        vec_fwd<Ar>(P, sm, LA, nullptr);
+    const long long Lk = TFT ? (static_cast<long long>(kb) << (logL - 4)) : L;   // positions kept
     for (long long idx = threadIdx.x; idx < (L << lppc); idx += blockDim.x) {
         const int v = static_cast<int>(idx >> logL);
         const long long i = idx & (L - 1);
+        if (TFT && i >= Lk) continue;
         const long long pa = vec_addr(LA, v, static_cast<int>(i)), pb = vec_addr(LA, v + ppc, static_cast<int>(i));
         sm[pa] = P.ar.mulmont(sm[pa], sm[pb]);
     }
     __syncthreads();
     const VecLayout LC = tile_layout(logL, lppc);
-    vec_inv<Ar>(P, sm, LC, nullptr);
+    if (TFT)
+        vec_inv_t<Ar>(P, sm, LC, kb, K);
+    else
+        vec_inv<Ar>(P, sm, LC, nullptr);
     const long long nc = na + nb - 1;
     for (long long idx = threadIdx.x; idx < (nc << lppc); idx += blockDim.x) {
         const int v = static_cast<int>(idx / nc);
@@ -186,13 +196,15 @@ k_tile_ntt(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long batch,
 // n/2 words, so the upper half of every column is zero padding.
 // KN nonzero: n = 2^KN and the block shape are fixed at compile time (the
 // runtime arguments must agree), so the index arithmetic of every pass
-// folds away.
-template <class Ar, bool ZHALF, int KN = 0, int LOGW = 0>
+// folds away.  TFT (k2 = 4 .. 8): only the rows of the kb column blocks
+// that the product's output needs are formed and stored (kb given for
+// uniform batches, from the descriptor's lengths for uneven ones).
+template <class Ar, bool ZHALF, int KN = 0, int LOGW = 0, bool TFT = false>
 __global__ void __launch_bounds__(kThreads)
 k_col_fwd(DevPlan<Ar> P, const typename Ar::word* src0, long long len0,
           const typename Ar::word* src1, long long len1, typename Ar::word* dst,
           long long dst_stride, long long dst_off1, int logN, int k2, int logw, long long prod_base,
-          const BatchDesc* __restrict__ desc) {
+          const BatchDesc* __restrict__ desc, int kb) {
     using word = typename Ar::word;
     if (KN) {
         logN = KN;
@@ -212,6 +224,7 @@ k_col_fwd(DevPlan<Ar> P, const typename Ar::word* src0, long long len0,
         const BatchDesc d = desc[prod];
         src = blockIdx.z ? src1 + d.boff : src0 + d.aoff;
         len = blockIdx.z ? d.nb : d.na;
+        if (TFT) kb = tft_kb(static_cast<long long>(d.na) + d.nb - 1, logN);
     } else {
         len = blockIdx.z ? len1 : len0;
         src = (blockIdx.z ? src1 : src0) + prod * len;
@@ -227,6 +240,17 @@ k_col_fwd(DevPlan<Ar> P, const typename Ar::word* src0, long long len0,
     }
     __syncthreads();
     Hook<Ar> h{P.glob_fwd, static_cast<int>(n1), 0, 1, static_cast<int>(c0)};
+    if (TFT) {
+        PhaseGeom g{k2, logw, 0, L.VS, 0, L.CS, true};
+        phase_fwd_t<Ar, ZHALF>(P, sm, g, &h, kb, TftConsts<Ar>{});   // the forward TFT needs no constants
+        const long long kept = (static_cast<long long>(kb) << (k2 - 4)) << logw;
+        for (long long idx = threadIdx.x; idx < kept; idx += blockDim.x) {
+            const long long row = idx >> logw;
+            const int col = static_cast<int>(idx & (w - 1));
+            out[row * n1 + c0 + col] = sm[vec_addr(L, col, static_cast<int>(row))];
+        }
+        return;
+    }
     vec_fwd<Ar, ZHALF>(P, sm, L, &h);        // ZHALF: the upper half of every column is padding
     for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const long long row = idx >> logw;
@@ -236,13 +260,15 @@ k_col_fwd(DevPlan<Ar> P, const typename Ar::word* src0, long long len0,
 }
 
 // Pass 3: inverse twiddle and inverse column transforms, scaled, cropped
-// store of the first out_len words of each product.
-template <class Ar, int KN = 0, int LOGW = 0>
+// store of the first out_len words of each product.  TFT (k2 = 4 .. 8):
+// only the rows of the kb kept column blocks are read; each column's outer
+// 16-point pass is solved by the inverse TFT with the zero rows above.
+template <class Ar, int KN = 0, int LOGW = 0, bool TFT = false>
 __global__ void __launch_bounds__(kThreads)
 k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
           typename Ar::word* dst, long long out_len, int logN, int k2, int logw,
           const typename Ar::tw* __restrict__ itab, long long prod_base,
-          const BatchDesc* __restrict__ desc) {
+          const BatchDesc* __restrict__ desc, int kb, TftConsts<Ar> K) {
     using word = typename Ar::word;
     if (KN) {
         logN = KN;
@@ -265,9 +291,11 @@ k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
     } else {
         outp = dst + prod * out_len;
     }
+    if (TFT) kb = tft_kb(out_len, logN);
     const VecLayout L = slab_layout(k2, logw);
     const long long total = (1LL << k2) << logw;
-    for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const long long loaded = TFT ? (static_cast<long long>(kb) << (k2 - 4)) << logw : total;
+    for (long long idx = threadIdx.x; idx < loaded; idx += blockDim.x) {
         const long long row = idx >> logw;
         const int col = static_cast<int>(idx & (w - 1));
         sm[vec_addr(L, col, static_cast<int>(row))] = in[row * n1 + c0 + col];
@@ -275,7 +303,12 @@ k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
     __syncthreads();
     // itab = inverse step-2 twiddles with the final scaling folded in
     Hook<Ar> h{itab, static_cast<int>(n1), 0, 1, static_cast<int>(c0)};
-    vec_inv<Ar>(P, sm, L, &h);
+    if (TFT) {
+        PhaseGeom g{k2, logw, 0, L.VS, 0, L.CS, true};
+        phase_inv_t<Ar>(P, sm, g, &h, kb, K);
+    } else {
+        vec_inv<Ar>(P, sm, L, &h);
+    }
     for (long long idx = threadIdx.x; idx < total; idx += blockDim.x) {
         const long long row = idx >> logw;
         const int col = static_cast<int>(idx & (w - 1));
@@ -287,10 +320,12 @@ k_col_inv(DevPlan<Ar> P, const typename Ar::word* src, long long src_stride,
 // Pass 2 of the product: rows of both transformed operands -> forward row
 // transforms, pointwise product, inverse row transforms of the product.
 // ws per product: [0, n) operand a, [n, 2n) operand b; result over a.
-template <class Ar, int KN = 0, int LRPC = 0>
+// TFT: blocks whose rows all lie past the kb kept column blocks of their
+// product (kb given, or from the descriptor's lengths) return at once.
+template <class Ar, int KN = 0, int LRPC = 0, bool TFT = false>
 __global__ void __launch_bounds__(kThreads)
 k_row_polymul(DevPlan<Ar> P, typename Ar::word* ws, long long ws_stride, int logN, int k2,
-              int lrpc, long long prod_base) {
+              int lrpc, long long prod_base, const BatchDesc* __restrict__ desc, int kb) {
     using word = typename Ar::word;
     if (KN) {
         logN = KN;
@@ -303,6 +338,13 @@ k_row_polymul(DevPlan<Ar> P, typename Ar::word* ws, long long ws_stride, int log
     const long long n1 = 1LL << k1, N = 1LL << logN;
     const int rpc = 1 << lrpc;
     const long long r0 = static_cast<long long>(blockIdx.x) << lrpc;
+    if (TFT) {
+        if (desc) {
+            const BatchDesc d = desc[prod_base + blockIdx.y];
+            kb = tft_kb(static_cast<long long>(d.na) + d.nb - 1, logN);
+        }
+        if (r0 >= (static_cast<long long>(kb) << (k2 - 4))) return;
+    }
     word* base = ws + (prod_base + blockIdx.y) * ws_stride;
     const VecLayout L = tile_layout(k1, lrpc + 1);
     const long long total = (2LL << lrpc) << k1;
@@ -371,7 +413,8 @@ k_row_ntt(DevPlan<Ar> P, typename Ar::word* data, int logN, int k2, int lrpc, lo
 // are copied into shared memory when the modulus changes.
 template <class Ar>
 __global__ void __launch_bounds__(kThreads)
-k_batch_small(const DevPlan<Ar>* __restrict__ plans, const BatchDesc* __restrict__ desc,
+k_batch_small(const DevPlan<Ar>* __restrict__ plans, const TftConsts<Ar>* __restrict__ tfts,
+              const BatchDesc* __restrict__ desc,
               const SmallItem<Ar>* __restrict__ items, unsigned nitems, unsigned* ticket,
               const typename Ar::word* __restrict__ a, const typename Ar::word* __restrict__ b,
               typename Ar::word* __restrict__ c) {
@@ -379,6 +422,7 @@ k_batch_small(const DevPlan<Ar>* __restrict__ plans, const BatchDesc* __restrict
     extern __shared__ __align__(16) unsigned char smraw[];
     word* sm = reinterpret_cast<word*>(smraw);
     __shared__ DevPlan<Ar> P;
+    __shared__ TftConsts<Ar> K;
     __shared__ BatchDesc sd[kSmallMaxPerItem];
     __shared__ unsigned s_item;
     __shared__ int s_prime;
@@ -395,6 +439,10 @@ k_batch_small(const DevPlan<Ar>* __restrict__ plans, const BatchDesc* __restrict
             unsigned* dst = reinterpret_cast<unsigned*>(&P);
             for (int i = threadIdx.x; i < static_cast<int>(sizeof(DevPlan<Ar>) / 4); i += blockDim.x)
                 dst[i] = src[i];
+            const unsigned* ksrc = reinterpret_cast<const unsigned*>(tfts + I.prime);
+            unsigned* kdst = reinterpret_cast<unsigned*>(&K);
+            for (int i = threadIdx.x; i < static_cast<int>(sizeof(TftConsts<Ar>) / 4); i += blockDim.x)
+                kdst[i] = ksrc[i];
         }
         if (threadIdx.x < I.count) sd[threadIdx.x] = desc[I.first + threadIdx.x];
         __syncthreads();
@@ -416,16 +464,26 @@ k_batch_small(const DevPlan<Ar>* __restrict__ plans, const BatchDesc* __restrict
             sm[vec_addr(LA, v + ppc, i)] = xb;
         }
         __syncthreads();
-        vec_fwd<Ar>(P, sm, LA, nullptr);
+        const int kb = static_cast<int>(I.kb);
+        const bool tft = kb < 16;                     // the plan sets 16 where truncation does not pay
+        if (tft)
+            vec_fwd_t<Ar>(P, sm, LA, kb, K);
+        else
+            vec_fwd<Ar>(P, sm, LA, nullptr);
+        const int Lk = tft ? (kb << (logL - 4)) : L;     // positions kept
         for (int idx = threadIdx.x; idx < (L << lppc); idx += blockDim.x) {
             const int v = idx >> logL;
             const int i = idx & (L - 1);
+            if (i >= Lk) continue;
             const int pa = vec_addr(LA, v, i), pb = vec_addr(LA, v + ppc, i);
             sm[pa] = P.ar.mulmont(sm[pa], sm[pb]);
         }
         __syncthreads();
         const VecLayout LC = tile_layout(logL, lppc);
-        vec_inv<Ar>(P, sm, LC, nullptr);
+        if (tft)
+            vec_inv_t<Ar>(P, sm, LC, kb, K);
+        else
+            vec_inv<Ar>(P, sm, LC, nullptr);
         for (int idx = threadIdx.x; idx < (L << lppc); idx += blockDim.x) {
             const int v = idx >> logL;
             const int i = idx & (L - 1);
@@ -1179,11 +1237,16 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
         const long long blocks = (batch + (1LL << lppc) - 1) >> lppc;
         const bool few = blocks < sm_count(plan->device);
         const bool wide = few || smem > kTileWideSmem;
-        auto kt = wide ? k_tile_polymul<Ar, 2 * kThreads> : k_tile_polymul<Ar, kThreads>;
+        // truncated transforms when the output leaves enough of the 16
+        // blocks of n/16 positions empty
+        const int kb = k >= kTileTftMinLog ? tft_kb(na + nb - 1, k) : 16;
+        const bool tft = kb <= kTileTftMaxBlocks;   // else the full transforms
+        auto kt = tft ? (wide ? k_tile_polymul<Ar, 2 * kThreads, true> : k_tile_polymul<Ar, kThreads, true>)
+                      : (wide ? k_tile_polymul<Ar, 2 * kThreads> : k_tile_polymul<Ar, kThreads>);
         int nt = wide ? 2 * kThreads : kThreads;
         if constexpr (sizeof(word) == 4) {
             if (few) {
-                kt = k_tile_polymul<Ar, 4 * kThreads>;
+                kt = tft ? k_tile_polymul<Ar, 4 * kThreads, true> : k_tile_polymul<Ar, 4 * kThreads>;
                 nt = 4 * kThreads;
             }
         }
@@ -1193,8 +1256,8 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
             const long long p0 = b0 << lppc;
             kt<<<static_cast<unsigned>(nb0), nt, smem, st>>>(
                 dp, a + p0 * na, na, b + p0 * nb, nb, c + p0 * (na + nb - 1), batch - p0, k, lppc,
-                scale);
-            prof_mark(st, "k_tile_polymul");
+                scale, kb, tft_consts<Ar>(plan));
+            prof_mark(st, tft ? "k_tile_polymul_tft" : "k_tile_polymul");
         }
         return check_launch("k_tile_polymul");
     }
@@ -1208,11 +1271,16 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
     const int lrpc = cfg.lrpc;
     const size_t smem_r = layout_words(tile_layout(k1, lrpc + 1)) * sizeof(word);
     const bool zhalf = 2 * std::max(na, nb) <= N;
-    auto kcf = zhalf ? k_col_fwd<Ar, true> : k_col_fwd<Ar, false>;
-    auto kci = k_col_inv<Ar>;
-    auto krp = k_row_polymul<Ar>;
+    // truncated transforms (columns of 16 .. 256 words) when the output
+    // leaves enough of the 16 column blocks empty
+    const int kb = (k2 >= 4 && k2 <= kMaxLineLog) ? tft_kb(na + nb - 1, k) : 16;
+    const bool tft = kb <= kColTftMaxBlocks;
+    auto kcf = tft ? (zhalf ? k_col_fwd<Ar, true, 0, 0, true> : k_col_fwd<Ar, false, 0, 0, true>)
+                   : (zhalf ? k_col_fwd<Ar, true> : k_col_fwd<Ar, false>);
+    auto kci = tft ? k_col_inv<Ar, 0, 0, true> : k_col_inv<Ar>;
+    auto krp = tft ? k_row_polymul<Ar, 0, 0, true> : k_row_polymul<Ar>;
     // compile-time geometry for the shape of the 2^16-point 32-bit products
-    if (sizeof(word) == 4 && k == 16 && logw == 5 && lrpc == 4) {
+    if (sizeof(word) == 4 && k == 16 && logw == 5 && lrpc == 4 && !tft) {
         kcf = zhalf ? k_col_fwd<Ar, true, 16, 5> : k_col_fwd<Ar, false, 16, 5>;
         kci = k_col_inv<Ar, 16, 5>;
         krp = k_row_polymul<Ar, 16, 4>;
@@ -1221,17 +1289,22 @@ int launch_polymul_fused(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
     if (allow_smem(kcf, smem_c) != cudaSuccess || allow_smem(kci, smem_c) != cudaSuccess ||
         allow_smem(krp, smem_r) != cudaSuccess)
         return check_launch("smem attr");
+    // rows of the row pass: the kept column blocks' rows, in whole blocks
+    // of 2^lrpc rows
+    const long long rows = tft ? (static_cast<long long>(kb) << (k2 - 4)) : (1LL << k2);
+    const unsigned row_blocks = static_cast<unsigned>((rows + (1LL << lrpc) - 1) >> lrpc);
     for (long long p0 = 0; p0 < batch; p0 += kMaxGridY) {
         const unsigned nbat = static_cast<unsigned>(std::min(batch - p0, kMaxGridY));
         dim3 gc(static_cast<unsigned>((1LL << k1) >> logw), nbat, 2);
-        kcf<<<gc, kThreads, smem_c, st>>>(dp, a, na, b, nb, ws, 2 * N, N, k, k2, logw, p0, nullptr);
-        prof_mark(st, "k_col_fwd");
-        dim3 gr(static_cast<unsigned>((1LL << k2) >> lrpc), nbat, 1);
-        krp<<<gr, kThreads, smem_r, st>>>(dp, ws, 2 * N, k, k2, lrpc, p0);
-        prof_mark(st, "k_row_polymul");
+        kcf<<<gc, kThreads, smem_c, st>>>(dp, a, na, b, nb, ws, 2 * N, N, k, k2, logw, p0, nullptr, kb);
+        prof_mark(st, tft ? "k_col_fwd_tft" : "k_col_fwd");
+        dim3 gr(row_blocks, nbat, 1);
+        krp<<<gr, kThreads, smem_r, st>>>(dp, ws, 2 * N, k, k2, lrpc, p0, nullptr, kb);
+        prof_mark(st, tft ? "k_row_polymul_tft" : "k_row_polymul");
         dim3 gi(static_cast<unsigned>((1LL << k1) >> logw), nbat, 1);
-        kci<<<gi, kThreads, smem_c, st>>>(dp, ws, 2 * N, c, na + nb - 1, k, k2, logw, itab, p0, nullptr);
-        prof_mark(st, "k_col_inv");
+        kci<<<gi, kThreads, smem_c, st>>>(dp, ws, 2 * N, c, na + nb - 1, k, k2, logw, itab, p0, nullptr, kb,
+                                          tft_consts<Ar>(plan));
+        prof_mark(st, tft ? "k_col_inv_tft" : "k_col_inv");
     }
     return check_launch("fused polymul passes");
 }
@@ -1263,14 +1336,14 @@ int launch_polymul_plain(const ntt_plan* plan, const DevPlan<Ar>& dp, const type
 }
 
 template <class Ar>
-int launch_batch_small(const DevPlan<Ar>* d_plans, const BatchDesc* d_desc, const void* d_items,
-                       unsigned nitems, unsigned* d_ticket, const typename Ar::word* a,
+int launch_batch_small(const DevPlan<Ar>* d_plans, const TftConsts<Ar>* d_tfts, const BatchDesc* d_desc,
+                       const void* d_items, unsigned nitems, unsigned* d_ticket, const typename Ar::word* a,
                        const typename Ar::word* b, typename Ar::word* c, size_t smem, int grid,
                        cudaStream_t st) {
     if (nitems == 0) return NTT_OK;
     if (allow_smem(k_batch_small<Ar>, smem) != cudaSuccess) return check_launch("smem attr");
     k_batch_small<Ar><<<grid, kThreads, smem, st>>>(
-        d_plans, d_desc, static_cast<const SmallItem<Ar>*>(d_items), nitems, d_ticket, a, b, c);
+        d_plans, d_tfts, d_desc, static_cast<const SmallItem<Ar>*>(d_items), nitems, d_ticket, a, b, c);
     prof_mark(st, "k_batch_small");
     return check_launch("k_batch_small");
 }
@@ -1289,7 +1362,7 @@ template <class Ar>
 int launch_batch_bucket(const ntt_plan* plan, const DevPlan<Ar>& dp, const typename Ar::word* a,
                         const typename Ar::word* b, typename Ar::word* c, const BatchDesc* d_desc,
                         long long count, typename Ar::word* ws, typename Ar::tw scale,
-                        cudaStream_t st, long long subs) {
+                        cudaStream_t st, long long subs, bool tft_bucket) {
     using word = typename Ar::word;
     const int k = static_cast<int>(plan->log2n);
     const LaunchCfg cfg = launch_cfg(sizeof(word), k, plan->tile_max_log);
@@ -1302,22 +1375,27 @@ int launch_batch_bucket(const ntt_plan* plan, const DevPlan<Ar>& dp, const typen
     const size_t smem_c = slab_words(slab_layout(k2, logw)) * sizeof(word);
     const size_t smem_r = layout_words(tile_layout(k1, lrpc + 1)) * sizeof(word);
     const auto* itab = static_cast<const typename Ar::tw*>(plan->glob_inv_pm);
-    if (allow_smem(k_col_fwd<Ar, false>, smem_c) != cudaSuccess ||
-        allow_smem(k_col_inv<Ar>, smem_c) != cudaSuccess ||
-        allow_smem(k_row_polymul<Ar>, smem_r) != cudaSuccess)
+    // a truncating bucket: every product runs the column blocks its own
+    // output needs
+    const bool tft = tft_bucket && k2 >= 4 && k2 <= kMaxLineLog;
+    auto kcf = tft ? k_col_fwd<Ar, false, 0, 0, true> : k_col_fwd<Ar, false>;
+    auto kci = tft ? k_col_inv<Ar, 0, 0, true> : k_col_inv<Ar>;
+    auto krp = tft ? k_row_polymul<Ar, 0, 0, true> : k_row_polymul<Ar>;
+    if (allow_smem(kcf, smem_c) != cudaSuccess || allow_smem(kci, smem_c) != cudaSuccess ||
+        allow_smem(krp, smem_r) != cudaSuccess)
         return check_launch("smem attr");
     for (long long p0 = 0; p0 < count; p0 += kMaxGridY) {
         const unsigned nbat = static_cast<unsigned>(std::min(count - p0, kMaxGridY));
         dim3 gc(static_cast<unsigned>((1LL << k1) >> logw), nbat, 2);
-        k_col_fwd<Ar, false><<<gc, kThreads, smem_c, st>>>(dp, a, 0, b, 0, ws, 2 * N, N, k, k2, logw, p0,
-                                                           d_desc);
-        prof_mark(st, "k_col_fwd");
+        kcf<<<gc, kThreads, smem_c, st>>>(dp, a, 0, b, 0, ws, 2 * N, N, k, k2, logw, p0, d_desc, 16);
+        prof_mark(st, tft ? "k_col_fwd_tft" : "k_col_fwd");
         dim3 gr(static_cast<unsigned>((1LL << k2) >> lrpc), nbat, 1);
-        k_row_polymul<Ar><<<gr, kThreads, smem_r, st>>>(dp, ws, 2 * N, k, k2, lrpc, p0);
-        prof_mark(st, "k_row_polymul");
+        krp<<<gr, kThreads, smem_r, st>>>(dp, ws, 2 * N, k, k2, lrpc, p0, d_desc, 16);
+        prof_mark(st, tft ? "k_row_polymul_tft" : "k_row_polymul");
         dim3 gi(static_cast<unsigned>((1LL << k1) >> logw), nbat, 1);
-        k_col_inv<Ar><<<gi, kThreads, smem_c, st>>>(dp, ws, 2 * N, c, 0, k, k2, logw, itab, p0, d_desc);
-        prof_mark(st, "k_col_inv");
+        kci<<<gi, kThreads, smem_c, st>>>(dp, ws, 2 * N, c, 0, k, k2, logw, itab, p0, d_desc, 16,
+                                          tft_consts<Ar>(plan));
+        prof_mark(st, tft ? "k_col_inv_tft" : "k_col_inv");
     }
     return check_launch("batch bucket passes");
 }
@@ -1497,7 +1575,7 @@ int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* d
         dim3 gr(static_cast<unsigned>((1LL << k2) >> lrpc), nbat, 1);
         if (fwd) {
             k_col_fwd<Ar, false><<<gc, kThreads, smem_c, st>>>(dp, data, N, data, N, data, N, 0, k, k2,
-                                                               logw, p0, nullptr);
+                                                               logw, p0, nullptr, 16);
             prof_mark(st, "k_col_fwd");
             krow<<<gr, kThreads, smem_r, st>>>(dp, data, k, k2, lrpc, p0);
             prof_mark(st, "k_row_ntt_fwd");
@@ -1505,7 +1583,7 @@ int launch_ntt(const ntt_plan* plan, const DevPlan<Ar>& dp, typename Ar::word* d
             krow<<<gr, kThreads, smem_r, st>>>(dp, data, k, k2, lrpc, p0);
             prof_mark(st, "k_row_ntt_inv");
             k_col_inv<Ar><<<gc, kThreads, smem_c, st>>>(dp, data, N, data, N, k, k2, logw, dp.glob_inv,
-                                                        p0, nullptr);
+                                                        p0, nullptr, 16, TftConsts<Ar>{});
             prof_mark(st, "k_col_inv");
         }
     }

@@ -9,12 +9,12 @@ template int launch_polymul_fused<Mont32>(const ntt_plan*, const DevPlan<Mont32>
 template int launch_polymul_plain<Mont32>(const ntt_plan*, const DevPlan<Mont32>&, const uint32_t*,
                                           long long, const uint32_t*, long long, long long, uint32_t*,
                                           uint32_t*, Tw32, cudaStream_t);
-template int launch_batch_small<Mont32>(const DevPlan<Mont32>*, const BatchDesc*, const void*, unsigned,
+template int launch_batch_small<Mont32>(const DevPlan<Mont32>*, const TftConsts<Mont32>*, const BatchDesc*, const void*, unsigned,
                                          unsigned*, const uint32_t*, const uint32_t*, uint32_t*, size_t, int,
                                          cudaStream_t);
 template int launch_batch_bucket<Mont32>(const ntt_plan*, const DevPlan<Mont32>&, const uint32_t*,
                                           const uint32_t*, uint32_t*, const BatchDesc*, long long,
-                                          uint32_t*, Tw32, cudaStream_t, long long);
+                                          uint32_t*, Tw32, cudaStream_t, long long, bool);
 template int batch_small_occupancy<Mont32>(size_t);
 template int launch_polymat<Mont32>(const ntt_plan*, const DevPlan<Mont32>&, const uint32_t*, const uint32_t*,
                                     int, long long, uint32_t*, uint32_t*, Tw32, Tw32, cudaStream_t);

@@ -42,7 +42,7 @@ size_t tile_smem_bytes(unsigned word_bytes, int logL, int lognvec) {
 LaunchCfg default_launch_cfg(unsigned word_bytes, int log2n, int tile_max_log) {
     LaunchCfg c{0, 0, 0};
     if (log2n <= tile_max_log) {
-        c.lppc = (log2n <= kMaxLineLog) ? 4 : 0;
+        c.lppc = small_lppc(log2n);
         return c;
     }
     if (log2n >= 2 * kDLog && log2n <= 3 * kDLog) return c;   // logw = 0: the direct kernels

@@ -62,6 +62,31 @@ def test_uneven_batch_u32_full():
         assert (got[t] == want[t]).all(), t
 
 
+@pytest.mark.parametrize("primes", [[W.P1, W.P2, W.P3], [W.P_A, W.P_B]])
+def test_uneven_batch_truncated_classes(primes):
+    """One product per (size 2^4 .. 2^15, class of kb blocks of n/16 output
+    positions): the persistent kernel's items and the two-pass buckets
+    truncate each transform to the blocks its output needs (Section 5.1);
+    every word against the oracle, graph capture and replay."""
+    g = W.SplitMix64(0x7B7 + len(primes))
+    la, lb = [], []
+    for k in range(4, 16):
+        n = 1 << k
+        for kb in (1, 3, 9, 12, 15, 16):
+            L = max(2, kb * n // 16 - (k % 3))
+            na = (L + 1) // 2 + (kb % 2)
+            la.append(na)
+            lb.append(L + 1 - na)
+    pidx = g.choice(len(primes), len(la))
+    a_list = [g.uniform_mod(primes[i], n) for i, n in zip(pidx, la)]
+    b_list = [g.uniform_mod(primes[i], n) for i, n in zip(pidx, lb)]
+    got = _run_batch(primes, a_list, b_list, pidx, runs=2)
+    want = O.polymul_ragged([primes[i] for i in pidx], a_list, b_list)
+    for r in range(2):
+        for t in range(len(want)):
+            assert (got[r][t] == want[t]).all(), (r, t, la[t], lb[t])
+
+
 @pytest.mark.parametrize("primes", [[W.P1, W.P3], [W.P_B, W.P_A]])
 def test_uneven_batch_2e16_bucket(primes):
     """Products whose transforms have 2^16 points (descriptor-driven direct

@@ -113,8 +113,8 @@ def test_config1_full_size_sampled(schedule):
         finally:
             G.ntt_tune_reset()
     _sampled_check(p, a.astype(np.uint64), b.astype(np.uint64), got, 64, 11)
-    # a few products in full against the schoolbook oracle
-    idx = [0, 255]
+    # eight products in full against the schoolbook oracle
+    idx = [0, 1, 37, 100, 128, 201, 254, 255]
     want = O.polymul_batch(p, a[idx].astype(np.uint64), b[idx].astype(np.uint64))
     assert (got[idx] == want).all()
 
@@ -206,6 +206,37 @@ def test_tft_products_every_length_class(p, beta):
         assert (tft[1] == O.polymul(p, a[1], b[1])).all()
     else:
         _sampled_check(p, a, b, tft, 24, beta)
+
+
+def _tft_lengths(log2n):
+    """Output lengths L <= n = 2^log2n at both ends of the classes of kb
+    blocks of n/16 positions (kb = 1, 2, 7, 9, 13, 14, 15, 16)."""
+    n = 1 << log2n
+    blk = n // 16
+    out = []
+    for kb in (1, 2, 7, 9, 13, 14, 15, 16):
+        out += [max(1, (kb - 1) * blk + 1), kb * blk]
+    return sorted(set(out))
+
+
+@pytest.mark.parametrize("p", [W.P_B, W.P1])
+@pytest.mark.parametrize("log2n", list(range(4, 16)))
+def test_tft_one_block_and_two_pass_sizes(p, log2n):
+    """Products through n = 2^4 .. 2^15 points -- the one-block kernel and,
+    above 2^14 (32-bit words) or 2^13 (64-bit), the two-pass kernels --
+    whose output needs kb of the 16 blocks of n/16 positions run the
+    truncated transforms of Section 5.1 (kb <= 14; the rest the full ones):
+    every output word against the schoolbook oracle, at both ends of each
+    class, with operands on both sides of n/2."""
+    g = W.SplitMix64(0x7F70 + log2n + p % 89)
+    for L in _tft_lengths(log2n):
+        na = max(1, min(L, (L + 1) // 2 + (L % 5) - 2))
+        nb = L + 1 - na
+        batch = 3 if log2n < 14 else 2
+        a = g.uniform_mod(p, batch * na).reshape(batch, na)
+        b = g.uniform_mod(p, batch * nb).reshape(batch, nb)
+        got = _polymul(p, log2n, a, b)
+        assert (got == O.polymul_batch(p, a, b)).all(), (log2n, L, na, nb)
 
 
 def _generic_vs_default(p, log2n, a, b):
