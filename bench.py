@@ -1088,6 +1088,22 @@ def run_suite(args, world, rank, local):
                             "peak_basis": "152 SMs x 64 lanes x 2070 MHz; one wide multiply-add per term"})
         del A, B, C, ws
 
+    # one integer product of two equal operands (three 62-bit primes, minimal-d
+    # chunks, Garner CRT, carry) at 2^20 .. 2^26 bits
+    g = W.SplitMix64(W.SEED_BASE + 16)
+    rows = []
+    with G.IntmulPlan(1 << 21) as plan:
+        for bits in (20, 22, 24, 26):
+            nl = (1 << bits) // 32
+            A = torch.from_numpy(g.limbs(nl)).to(dev)
+            B = torch.from_numpy(g.limbs(nl)).to(dev)
+            C = torch.empty(2 * nl, dtype=torch.uint32, device=dev)
+            ws = torch.empty(G.intmul_workspace_size(plan, nl, nl), dtype=torch.uint8, device=dev)
+            ms = med(lambda: G.intmul_crt(plan, A, nl, B, nl, C, ws, stream=stream), 10)
+            rows.append({"bits": 1 << bits, "ms": round(ms, 4)})
+            del A, B, C, ws
+    emit("one integer product of two equal operands (three 62-bit primes)", rows=rows)
+
     # integer matrix product, n = 32, entries of 2^15 limbs (Table 17's shape)
     n, na = 32, 1 << 15
     g = W.SplitMix64(W.SEED_BASE + 17)

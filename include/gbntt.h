@@ -374,10 +374,12 @@ size_t intmul_workspace_size(const intmul_plan* plan, size_t na, size_t nb);
 
 /* c = a * b for non-negative integers in little-endian 32-bit limbs:
  * a has na >= 1 limbs, b has nb >= 1, c receives exactly na + nb limbs.
- * Kronecker segmentation into h = 64-bit chunks, the product modulo each of
+ * Kronecker segmentation into chunks of Section 5.3's size h, the largest
+ * h <= 96 with 2 h + bitlength(min(da, db)) <= 183 (da, db the chunk counts;
+ * 80 to 91 bits at 2^14 .. 2^28-bit operands), the product modulo each of
  * the three primes (two forward transforms, pointwise product, inverse),
  * Garner reconstruction of every coefficient (exact: coefficients are below
- * 2^150 < P1 P2 P3) and carry propagation (Section 5.3).  d_ws: at least
+ * 2^183 < P1 P2 P3) and carry propagation.  d_ws: at least
  * intmul_workspace_size bytes, 256-byte aligned.  Asynchronous on stream. */
 int intmul_crt(const intmul_plan* plan, const uint32_t* d_a, size_t na, const uint32_t* d_b,
                size_t nb, uint32_t* d_c, void* d_ws, size_t ws_bytes, void* stream);
