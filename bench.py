@@ -311,6 +311,27 @@ def time_oracle(p, a, b, target_s: float = 12.0):
     return count / dt, cores, sample, prods
 
 
+def time_cpu_ntt(p, a, b, target_s: float = 3.0):
+    """The textbook radix-2 transform product (oracle/cpu_ntt.c, the
+    O(n log n) CPU reference) on a bounded sample of the workload's products,
+    on this host's cores.  Returns (products/s, cores, sample text, products)."""
+    import numpy as np
+    import oracle as O
+    cores = O.num_threads()
+    k = min(a.shape[0], cores)
+    t0 = time.perf_counter()
+    O.ntt_polymul_batch(p, a[:k].astype(np.uint64), b[:k].astype(np.uint64))
+    one_round = time.perf_counter() - t0
+    count = int(max(k, min(a.shape[0], k * target_s / max(one_round, 1e-6))))
+    t0 = time.perf_counter()
+    prods = O.ntt_polymul_batch(p, a[:count].astype(np.uint64), b[:count].astype(np.uint64))
+    dt = time.perf_counter() - t0
+    sample = (f"{count} of the {a.shape[0]} products (textbook radix-2 transforms of "
+              f"{1 << (a.shape[1] + b.shape[1] - 2).bit_length()} points, u128 remainders), "
+              f"{dt:.2f} s wall on {cores} threads")
+    return count / dt, cores, sample, prods
+
+
 def run_reference(args, world, rank, target_s: float = 120.0):
     """The oracle (schoolbook) as the reference arm, on this host's cores.
     Each step is a bounded sample of the workload sized so that warm-up and
@@ -850,6 +871,12 @@ def run_native(args, world, rank, local):
         cpu = {"value": cv, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                "parity_checked_products": int(prods.shape[0]),
                "parity_ok": bool((got == prods).all())}
+        nv, ncores, nsample, nprods = time_cpu_ntt(p, a, b)
+        ngot = dc.view(batch, nc)[:nprods.shape[0]].cpu().numpy().astype(np.uint64)
+        cpu["ntt_reference"] = {"value": nv, "unit": UNIT, "cores": ncores,
+                                "kind": "textbook radix-2 transform product (O(n log n) CPU reference)",
+                                "sample": nsample, "equals_device_result": bool((ngot == nprods).all()),
+                                "gpu_over_cpu_ntt": value / nv}
 
     if rank != 0:
         plan.close()

@@ -17,6 +17,11 @@ Hoeven, Lecerf and Quintin, "Modular SIMD arithmetic in Mathemagix" (2014):
   (Section 5.3's integer product);
 * ``is_prime``, ``least_generator``, ``root_of_unity``, ``find_prime`` --
   the moduli p = k 2^l + 1 and their roots of unity (Sections 1, 5.1).
+
+``cpu_ntt.c`` (same library) adds ``ntt_polymul_batch``: the textbook
+radix-2 transform product, the O(n log n) CPU reference that the benchmark
+times beside the schoolbook oracle.  It is not a parity oracle; the tests pin
+it to the schoolbook product.
 """
 from __future__ import annotations
 
@@ -28,7 +33,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "cpu_ntt.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -41,14 +46,14 @@ _p32 = ctypes.POINTER(ctypes.c_uint32)
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into _build/liboracle.so with gcc (OpenMP on)."""
+    """Compile oracle.c and cpu_ntt.c into _build/liboracle.so with gcc (OpenMP on)."""
     os.makedirs(_BUILD, exist_ok=True)
     stale = (not os.path.exists(_LIB_PATH)
-             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+             or os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(s) for s in _SRCS))
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC",
-                               "-o", tmp, _SRC])
+                               "-o", tmp] + _SRCS)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -83,6 +88,7 @@ def _load():
             "orc_polymat_mul": (None, [_u64, _p64, _p64, _sz, _sz, _p64]),
             "orc_mulmod_vec": (None, [_u64, _p64, _p64, _sz, _p64]),
             "orc_num_threads": (ctypes.c_int, []),
+            "orc_ntt_polymul_batch": (ctypes.c_int, [_u64, _p64, _sz, _p64, _sz, _sz, _p64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -219,6 +225,22 @@ def polymul_batch(p: int, a, b) -> np.ndarray:
     assert count == count2
     c = np.empty((count, na + nb - 1), dtype=np.uint64)
     _load().orc_polymul_batch(p, _ptr64(a), na, _ptr64(b), nb, count, _ptr64(c))
+    return c
+
+
+def ntt_polymul_batch(p: int, a, b) -> np.ndarray:
+    """a: (count, na), b: (count, nb) -> (count, na+nb-1) through the textbook
+    radix-2 transform product (cpu_ntt.c), OpenMP over products.  The CPU
+    timing reference; parity is checked against polymul_batch."""
+    a = _u64arr(a)
+    b = _u64arr(b)
+    count, na = a.shape
+    count2, nb = b.shape
+    assert count == count2
+    c = np.empty((count, na + nb - 1), dtype=np.uint64)
+    rc = _load().orc_ntt_polymul_batch(p, _ptr64(a), na, _ptr64(b), nb, count, _ptr64(c))
+    if rc != 0:
+        raise MemoryError("orc_ntt_polymul_batch: scratch allocation failed")
     return c
 
 

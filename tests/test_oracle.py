@@ -438,3 +438,21 @@ def test_polymat_mul_entry_sums():
             for l in range(n):
                 acc = acc + O.polymul(p, A[i, l], B[l, j]).astype(object)
             assert (C[i, j].astype(object) == acc % p).all()
+
+
+@pytest.mark.parametrize("p", [W.P_A, W.P_B, W.P1, 17])
+def test_cpu_ntt_reference_equals_schoolbook(p):
+    """The O(n log n) CPU reference (cpu_ntt.c, timed by the benchmark) gives
+    the schoolbook products word for word: ragged and degree-0 operands,
+    sizes from one word to 2^12 points, and all-(p-1) operands."""
+    g = W.SplitMix64(0xC0DE + p % 1009)
+    shapes = [(1, 1), (1, 7), (3, 5), (16, 17), (100, 29), (1024, 1024), (2048, 2047)]
+    if p == 17:                                  # 17 - 1 = 2^4: transforms of at most 16 points
+        shapes = [(1, 1), (2, 3), (8, 9), (5, 12)]
+    for na, nb in shapes:
+        a = g.uniform_mod(p, 3 * na).reshape(3, na)
+        b = g.uniform_mod(p, 3 * nb).reshape(3, nb)
+        assert (O.ntt_polymul_batch(p, a, b) == O.polymul_batch(p, a, b)).all(), (p, na, nb)
+    n = 8 if p == 17 else 512
+    a = np.full((1, n), p - 1, dtype=np.uint64)
+    assert (O.ntt_polymul_batch(p, a, a) == O.polymul_batch(p, a, a)).all()
