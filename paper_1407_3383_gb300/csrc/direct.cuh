@@ -44,6 +44,7 @@ static_assert(kDItems * kDGroups == 16, "column blocks cover 16 x 16 lines");
 // one block per SM) made their column pass 37% faster.
 constexpr int kDColMinBlocks = 4;
 constexpr int kDColMinBlocks64 = 2;   // 64-bit words: up to 128 registers
+constexpr int kDColInvMinBlocks64 = 3;   // the inverse column pass fits 3 blocks (up to 85) without spilling
 
 __host__ __device__ constexpr size_t direct_col_smem_words() { return size_t(kDCols) * kDLine; }
 
@@ -334,17 +335,35 @@ k_row_polymul_d(DevPlan<Ar> P, const typename WideForm<Ar>::type ar, typename Ar
     // outer forward pass of row r of operand i (line RPB i + r)
     const tw* lf = P.line256_t[0];
     const uint32_t* lf_w = P.wline_t[0];
+    if constexpr (sizeof(word) == 8) {
+        // 64-bit words: the two operands' passes unrolled together (more
+        // independent work per thread; measured 0.326 -> 0.309 ms for 256
+        // products, while 32-bit words ran 21% slower that way)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const word* in = base + i * N + static_cast<long long>(r0 + r) * kDLine + j1;
+            word x[16];
+#pragma unroll
+            for (int t = 0; t < 16; ++t) x[t] = in[16 * t];
+            dif_regs<Ax, 16>(ar, x, P.rc);
+#pragma unroll
+            for (int t = 1; t < 16; ++t) x[t] = ar.mulw(x[t], tw_at(ar, lf, lf_w, t * 16 + j1));
+#pragma unroll
+            for (int t = 0; t < 16; ++t) sm[RL::at(RPB * i + r, 16 * t + j1)] = x[t];
+        }
+    } else {
 #pragma unroll 1
-    for (int i = 0; i < 2; ++i) {
-        const word* in = base + i * N + static_cast<long long>(r0 + r) * kDLine + j1;
-        word x[16];
+        for (int i = 0; i < 2; ++i) {
+            const word* in = base + i * N + static_cast<long long>(r0 + r) * kDLine + j1;
+            word x[16];
 #pragma unroll
-        for (int t = 0; t < 16; ++t) x[t] = in[16 * t];
-        dif_regs<Ax, 16>(ar, x, P.rc);
+            for (int t = 0; t < 16; ++t) x[t] = in[16 * t];
+            dif_regs<Ax, 16>(ar, x, P.rc);
 #pragma unroll
-        for (int t = 1; t < 16; ++t) x[t] = ar.mulw(x[t], tw_at(ar, lf, lf_w, t * 16 + j1));
+            for (int t = 1; t < 16; ++t) x[t] = ar.mulw(x[t], tw_at(ar, lf, lf_w, t * 16 + j1));
 #pragma unroll
-        for (int t = 0; t < 16; ++t) sm[RL::at(RPB * i + r, 16 * t + j1)] = x[t];
+            for (int t = 0; t < 16; ++t) sm[RL::at(RPB * i + r, 16 * t + j1)] = x[t];
+        }
     }
     __syncthreads();
     // inner passes of both operands, pointwise product, inner inverse pass
@@ -436,7 +455,7 @@ k_row_ntt_d(DevPlan<Ar> P, typename Ar::word* __restrict__ data, long long prod_
 // (B known outputs, known zero inputs above them), scaled like the other
 // unnormalised passes.
 template <class Ar, bool TFT = false>
-__global__ void __launch_bounds__(kDThreads, sizeof(typename Ar::word) == 4 ? kDColMinBlocks : kDColMinBlocks64)
+__global__ void __launch_bounds__(kDThreads, sizeof(typename Ar::word) == 4 ? kDColMinBlocks : kDColInvMinBlocks64)
 k_col_inv_d(DevPlan<Ar> P, const typename WideForm<Ar>::type ar, const typename Ar::word* __restrict__ src,
             long long src_stride,
             typename Ar::word* __restrict__ dst, long long out_len, long long dst_stride,
