@@ -138,7 +138,7 @@ int build_device_block(polymul_batch_plan* B, const std::vector<BatchDesc>& desc
 // returns the descriptors in execution order.
 template <class Ar, class TwOf>
 int plan_products(polymul_batch_plan* B, const polymul_desc* h, size_t count, TwOf tw_of) {
-    const int tile_max = (B->wb == 4) ? 14 : 13;
+    const int tile_max = (B->wb == 4) ? kTileMaxLog32 : kTileMaxLog64;
     struct Ent {
         size_t idx;
         int k;

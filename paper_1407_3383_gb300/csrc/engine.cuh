@@ -37,6 +37,10 @@
 namespace gbntt {
 
 constexpr int kMaxLineLog = 8;      // lines are at most 256 words
+// Largest transform (log2) that one thread block holds whole, both operands
+// resident in shared memory: 32-bit and 64-bit words.
+constexpr int kTileMaxLog32 = 13;
+constexpr int kTileMaxLog64 = 13;
 
 // Per-modulus constants and table pointers, passed by value to every kernel
 // (so they sit in the constant bank).

@@ -508,7 +508,7 @@ extern "C" int ntt_plan_create(uint64_t p, unsigned log2n, unsigned flags, ntt_p
     P->omega = pow_mod(P->g, (p - 1) >> log2n, p);
     P->omega_inv = pow_mod(P->omega, p - 2, p);
     P->n_inv = pow_mod((1ull << log2n) % p, p - 2, p);
-    P->tile_max_log = (P->word_bytes == 4) ? 14 : 13;
+    P->tile_max_log = (P->word_bytes == 4) ? kTileMaxLog32 : kTileMaxLog64;
     P->k2 = static_cast<int>(log2n) / 2;
     P->k1 = static_cast<int>(log2n) - P->k2;
     if (cudaGetDevice(&P->device) != cudaSuccess) {

@@ -213,7 +213,7 @@ extern "C" int ntt_autotune(const ntt_plan* plan, size_t batch, void* stream, fl
 
 extern "C" int ntt_tune_get(unsigned word_bytes, unsigned log2n, int* lppc, int* logw, int* lrpc) {
     if (!lppc || !logw || !lrpc || (word_bytes != 4 && word_bytes != 8)) return NTT_ERR_ARG;
-    const LaunchCfg c = launch_cfg(word_bytes, static_cast<int>(log2n), word_bytes == 4 ? 14 : 13);
+    const LaunchCfg c = launch_cfg(word_bytes, static_cast<int>(log2n), word_bytes == 4 ? kTileMaxLog32 : kTileMaxLog64);
     *lppc = c.lppc;
     *logw = c.logw;
     *lrpc = c.lrpc;

@@ -44,7 +44,8 @@ def test_config0_single_product_full():
     (W.P_B, 5, 17, 16, 19),        # short vectors, many per block, ragged batch
     (W.P_A, 8, 128, 129, 33),      # one-line vectors at the 256 limit
     (W.P_B, 9, 300, 200, 5),       # first tiled size
-    (W.P_B, 14, 8192, 8192, 2),    # largest one-block tile (u32)
+    (W.P_B, 13, 4096, 4096, 3),    # largest one-block tile (u32)
+    (W.P_B, 14, 8192, 8192, 2),    # two global passes (u32), both operands half the transform
     (W.P_B, 15, 9000, 7001, 2),    # two global passes, ragged lengths
     (W.P_A, 16, 1 << 15, 1 << 15, 2),
     (W.P_B, 16, 40000, 25535, 3),  # 2^16 points, operand a past n/2: no zero half
@@ -223,7 +224,7 @@ def _tft_lengths(log2n):
 @pytest.mark.parametrize("log2n", list(range(4, 16)))
 def test_tft_one_block_and_two_pass_sizes(p, log2n):
     """Products through n = 2^4 .. 2^15 points -- the one-block kernel and,
-    above 2^14 (32-bit words) or 2^13 (64-bit), the two-pass kernels --
+    above 2^13 points, the two-pass kernels --
     whose output needs kb of the 16 blocks of n/16 positions run the
     truncated transforms of Section 5.1 (kb <= 14; the rest the full ones):
     every output word against the schoolbook oracle, at both ends of each
