@@ -183,9 +183,12 @@ struct Shoup64L {
     uint64_t p;      // modulus < 2^62
     uint64_t pinv;   // p^-1 rem 2^64
 
-    __device__ __forceinline__ uint64_t red2(uint64_t s) const {   // s < 4p -> [0, 2p)
+    // s < 4p -> [0, 2p).  t = s - 2p read as a signed 64-bit value is
+    // negative exactly when s < 2p (2p - s <= 2p < 2^63), so the choice
+    // needs the sign of t's high word only, not a 64-bit comparison.
+    __device__ __forceinline__ uint64_t red2(uint64_t s) const {
         const uint64_t t = s - 2 * p;
-        return (s >= 2 * p) ? t : s;
+        return (static_cast<int64_t>(t) < 0) ? s : t;
     }
     __device__ __forceinline__ uint64_t add(uint64_t x, uint64_t y) const { return red2(x + y); }
     __device__ __forceinline__ uint64_t sub(uint64_t x, uint64_t y) const { return red2(x + 2 * p - y); }
@@ -199,10 +202,14 @@ struct Shoup64L {
         const uint64_t hi = __umul64hi(x, y);
         const uint64_t q = lo * pinv;
         const uint64_t l = __umul64hi(q, p);
-        const uint64_t r = hi - l;
-        return (hi >= l) ? r : r + p;
+        const uint64_t r = hi - l;                       // hi, l < p < 2^62: negative iff hi < l
+        return (static_cast<int64_t>(r) < 0) ? r + p : r;
     }
-    __device__ __forceinline__ uint64_t canon(uint64_t x) const { return (x >= p) ? x - p : x; }
+    // [0, 2p) -> [0, p), with the same sign test
+    __device__ __forceinline__ uint64_t canon(uint64_t x) const {
+        const uint64_t t = x - p;
+        return (static_cast<int64_t>(t) < 0) ? x : t;
+    }
 };
 
 // Fma50 -- residues as IEEE doubles, p < 2^50 (m <= l - 2 with l = 53 for
