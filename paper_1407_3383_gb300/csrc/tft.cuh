@@ -243,7 +243,7 @@ __device__ __forceinline__ void itft16_z16(const Ar& ar, typename Ar::word (&x)[
 // final scaling by n^-1 is unchanged.
 
 // Products whose output needs few enough of the 16 blocks run truncated
-// transforms: one-block tiles (n = 2^9 .. 2^14) at most kTileTftMaxBlocks,
+// transforms: one-block tiles (n = 2^9 .. 2^13) at most kTileTftMaxBlocks,
 // the two-pass sizes below 2^16 at most kColTftMaxBlocks.  Measured on 2^23
 // output words per call, time against the full transforms at kb = 9 / 12:
 // tiles 0.80 .. 1.0 / 0.95 .. 1.05, two-pass 0.77 .. 0.82 / 0.88 .. 0.96;
