@@ -47,18 +47,19 @@ OPS32 = {"add": 3, "sub": 3, "mulw": 6, "mulg": 7}
 # 32-bit-instruction counts of the 64-bit word policy's forms (Shoup64L,
 # p < 2^62, lazy residues in [0, 2p)), from their decomposition into 32-bit
 # instructions: a 64-bit add or subtract is 2 (low word with carry, high
-# word); a 64-bit unsigned compare 2; a 64-bit select 2; the low 64 bits of
-# a 64 x 64 product 3 (one wide multiply and two multiply-adds into the high
-# word); the high 64 bits 6 (the high word of the low partial product, three
-# wide multiply-adds with 64-bit addends, one 64-bit add).
-#   add      red2(x + y): add 2, then s - 2p, compare, select: 8
-#   sub      red2(x + 2p - y) (one three-input add per word): 8
+# word); the sign test of a 64-bit difference 1 (its high word); a 64-bit
+# select 2; the low 64 bits of a 64 x 64 product 3 (one wide multiply and
+# two multiply-adds into the high word); the high 64 bits 6 (the high word
+# of the low partial product, three wide multiply-adds with 64-bit addends,
+# one 64-bit add).
+#   add      red2(x + y): add 2, then t = s - 2p 2, sign of t 1, select 2: 7
+#   sub      red2(x + 2p - y) (one three-input add per word): 7
 #   sub_lazy x + 2p - y, feeding a twiddle product: 2
 #   mulw     Function 8: high product 6, two low products 6, subtract 2: 14
 #   mulg     Montgomery: 128-bit product 8, q = lo p' 3, high product 6,
-#            subtract 2, compare 2, corrected select 4: 25
-#   canon    [0, 2p) -> [0, p): compare 2, subtract 2, select 2: 6
-OPS64 = {"add": 8, "sub": 8, "sub_lazy": 2, "mulw": 14, "mulg": 25, "canon": 6}
+#            subtract 2, sign 1, corrected select 4: 24
+#   canon    [0, 2p) -> [0, p): subtract 2, sign 1, select 2: 5
+OPS64 = {"add": 7, "sub": 7, "sub_lazy": 2, "mulw": 14, "mulg": 24, "canon": 5}
 
 
 def parse():
@@ -73,7 +74,8 @@ def parse():
                     help="run only the fused timed steps (for profiler captures)")
     ap.add_argument("--workload", default="polymul",
                     choices=["polymul", "serve", "modmul", "suite", "fp64", "tft", "single_product",
-                             "transform_2e24_u64", "products_2e12_u64", "uneven_10000", "serving"],
+                             "transform_2e24_u64", "products_2e12_u64", "products_2e16_u64", "uneven_10000",
+                             "serving"],
                     help="polymul: the batched product (headline); serve: the Poisson "
                          "stream of integer products through the serving loop; modmul: "
                          "throughput of each reduction; suite: the other workloads and the "
@@ -81,7 +83,8 @@ def parse():
                          "doubles (Function 16) against the integer ones at Table 12's sizes; "
                          "tft: 2^16-point products by output length class (truncated "
                          "transforms against the full length); single_product, "
-                         "transform_2e24_u64, products_2e12_u64, uneven_10000, serving: one of "
+                         "transform_2e24_u64, products_2e12_u64, products_2e16_u64, uneven_10000, "
+                         "serving: one of "
                          "the workloads the default line carries, alone (profiler captures)")
     ap.add_argument("--requests", type=int, default=48, help="serve: requests per stream")
     ap.add_argument("--no-autotune", action="store_true",
@@ -498,6 +501,7 @@ def run_workloads(G, dev, stream, flush, peak_gops: float, hbm: float, only=None
         "single_product": lambda: wl_single_product(G, dev, stream, med, flush, peak_gops),
         "transform_2e24_u64": lambda: wl_transform_2e24(G, dev, stream, med, peak_gops, hbm),
         "products_2e12_u64": lambda: wl_products_2e12(G, dev, stream, med, peak_gops, hbm),
+        "products_2e16_u64": lambda: wl_products_2e16(G, dev, stream, med, peak_gops, hbm),
         "uneven_10000": lambda: uneven_batch(G, dev, stream, flush, med),
         "serving": lambda: serve_closed_loop(G, requests=48),
     }
@@ -592,6 +596,39 @@ def wl_products_2e12(G, dev, stream, med, peak_gops: float, hbm: float) -> dict:
             "config": {"workload": "1024 products 2^12 x 2^12 mod P1 (62-bit), 2^13-point NTTs, u64",
                        "l2": "flushed before each call"},
             "metric": "products/s", "value": 1024 / (ms * 1e-3), "unit": "products/s", "higher_is_better": True,
+            "ms": ms, "roofline": alu_roofline(ops, ms * 1e-3, peak_gops),
+            "hbm": hbm_roofline(nbytes, ms * 1e-3, hbm),
+            "oracle_checked_products": len(sel), "matches_oracle": ok}
+
+
+def wl_products_2e16(G, dev, stream, med, peak_gops: float, hbm: float) -> dict:
+    """256 products of length 2^15 mod P1 (2^16 points, u64): the direct
+    256 x 256 kernels with 64-bit words, the stage that dominates the uneven
+    batch (its 2^16-point products and the rows of its longer ones)."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_1407_3383_gb300 import workloads as W
+    p, batch, n = W.P1, 256, 1 << 15
+    g = W.SplitMix64(W.SEED_BASE + 21)
+    a = g.uniform_mod(p, batch * n).reshape(batch, n)
+    b = g.uniform_mod(p, batch * n).reshape(batch, n)
+    with G.Plan(p, 16) as plan:
+        da = torch.from_numpy(a.reshape(-1)).to(dev)
+        db = torch.from_numpy(b.reshape(-1)).to(dev)
+        dc = torch.empty(batch * (2 * n - 1), dtype=torch.uint64, device=dev)
+        ws = G.alloc_workspace(plan, batch)
+        ms = med(lambda: G.polymul_mod_p_batch(plan, da, n, db, n, batch, dc, G.NTT_SCHED_FUSED, ws,
+                                               stream=stream), 20)
+        sel = [0, batch - 1]
+        want = O.polymul_batch(p, a[sel], b[sel])
+        ok = bool((dc.view(batch, 2 * n - 1).cpu().numpy()[sel] == want).all())
+        ops = polymul64_ops(16, n, n, batch)
+        nbytes = batch * (4 * n - 1) * 8
+        return {
+            "config": {"workload": "256 products 2^15 x 2^15 mod P1 (62-bit), 2^16-point NTTs, u64",
+                       "l2": "flushed before each call"},
+            "metric": "products/s", "value": batch / (ms * 1e-3), "unit": "products/s", "higher_is_better": True,
             "ms": ms, "roofline": alu_roofline(ops, ms * 1e-3, peak_gops),
             "hbm": hbm_roofline(nbytes, ms * 1e-3, hbm),
             "oracle_checked_products": len(sel), "matches_oracle": ok}
@@ -1265,8 +1302,8 @@ def main():
         run_fp64(args, world, rank, local)
     elif args.workload == "tft" and args.impl == "native":
         run_tft(args, world, rank, local)
-    elif args.workload in ("single_product", "transform_2e24_u64", "products_2e12_u64", "uneven_10000",
-                           "serving") and args.impl == "native":
+    elif args.workload in ("single_product", "transform_2e24_u64", "products_2e12_u64", "products_2e16_u64",
+                           "uneven_10000", "serving") and args.impl == "native":
         run_one_workload(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)
