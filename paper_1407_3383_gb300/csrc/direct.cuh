@@ -39,11 +39,12 @@ static_assert(kDItems * kDGroups == 16, "column blocks cover 16 x 16 lines");
 // Column blocks per SM the compiler must fit with 32-bit words: 4 leaves up
 // to 64 registers a thread, which measured 4% faster per product step than
 // the 32-48 the compiler picks unbounded (more loads in flight per thread).
-// 64-bit words would spill under that bound; 2 blocks (up to 128 registers
-// instead of the 168 the compiler picks for the full column pass, which left
-// one block per SM) made their column pass 37% faster.
+// 64-bit words would spill under that bound.  For them 3 blocks (up to 85
+// registers, with the step-2 twiddles loaded and applied in two halves) run
+// the column pass 5% faster than 2 blocks (128 registers), which in turn
+// were 37% faster than the 168 registers the compiler picks unbounded.
 constexpr int kDColMinBlocks = 4;
-constexpr int kDColMinBlocks64 = 2;   // 64-bit words: up to 128 registers
+constexpr int kDColMinBlocks64 = 3;   // 64-bit words: up to 85 registers (step-2 twiddles in two halves)
 constexpr int kDColInvMinBlocks64 = 3;   // the inverse column pass fits 3 blocks (up to 85) without spilling
 
 __host__ __device__ constexpr size_t direct_col_smem_words() { return size_t(kDCols) * kDLine; }
@@ -172,12 +173,18 @@ k_col_fwd_d(DevPlan<Ar> P, const Ar ar, const typename Ar::word* __restrict__ sr
 #pragma unroll
         for (int t = 0; t < 16; ++t) x[t] = sm[(16 * blk + t) * kDCols + v];
         dif_regs<Ar, 16>(ar, x, P.rc);
-        if constexpr (sizeof(word) != 4) {            // wider words: after it (register pressure)
+        if constexpr (sizeof(word) != 4) {            // wider words: after it, in two halves (register pressure)
 #pragma unroll
-            for (int t = 0; t < 16; ++t) w[t] = tw_at(ar, gt, gt_w, (16 * blk + t) * kDLine);
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int t = 8 * h; t < 8 * h + 8; ++t) w[t] = tw_at(ar, gt, gt_w, (16 * blk + t) * kDLine);
+#pragma unroll
+                for (int t = 8 * h; t < 8 * h + 8; ++t) out[(16 * blk + t) * kDLine] = ar.mulw(x[t], w[t]);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 16; ++t) out[(16 * blk + t) * kDLine] = ar.mulw(x[t], w[t]);
         }
-#pragma unroll
-        for (int t = 0; t < 16; ++t) out[(16 * blk + t) * kDLine] = ar.mulw(x[t], w[t]);
     }
 }
 
@@ -295,7 +302,7 @@ struct RowLayout {
 
 constexpr int kDRowsPerBlock = 4;      // rows of each operand per row block (64 threads)
 constexpr int kDRowMinBlocks32 = 16;   // 32-bit words: 16 blocks per SM (up to 64 registers)
-constexpr int kDRowMinBlocks64 = 8;   // 64-bit words: up to 128 registers
+constexpr int kDRowMinBlocks64 = 10;  // 64-bit words: up to 96 registers (half the line twiddles live at once)   // 64-bit words: up to 128 registers
 constexpr int kDNttRowsPerBlock = 8;   // standalone row transforms (128 threads)
 constexpr int kDTftMaxBlocks = 13;     // uniform batches needing more row blocks run the full kernels
 
@@ -347,7 +354,10 @@ k_row_polymul_d(DevPlan<Ar> P, const typename WideForm<Ar>::type ar, typename Ar
             for (int t = 0; t < 16; ++t) x[t] = in[16 * t];
             dif_regs<Ax, 16>(ar, x, P.rc);
 #pragma unroll
-            for (int t = 1; t < 16; ++t) x[t] = ar.mulw(x[t], tw_at(ar, lf, lf_w, t * 16 + j1));
+            for (int t = 1; t < 16; ++t) {
+                if (t == 8) asm volatile("" ::: "memory");   // at most half the twiddles live
+                x[t] = ar.mulw(x[t], tw_at(ar, lf, lf_w, t * 16 + j1));
+            }
 #pragma unroll
             for (int t = 0; t < 16; ++t) sm[RL::at(RPB * i + r, 16 * t + j1)] = x[t];
         }
@@ -390,7 +400,10 @@ k_row_polymul_d(DevPlan<Ar> P, const typename WideForm<Ar>::type ar, typename Ar
 #pragma unroll
         for (int t = 0; t < 16; ++t) x[t] = sm[RL::at(r, 16 * t + j1)];
 #pragma unroll
-        for (int t = 1; t < 16; ++t) x[t] = ar.mulw(x[t], tw_at(ar, li, li_w, t * 16 + j1));
+        for (int t = 1; t < 16; ++t) {
+            if (sizeof(word) == 8 && t == 8) asm volatile("" ::: "memory");   // 64-bit words: half the twiddles live
+            x[t] = ar.mulw(x[t], tw_at(ar, li, li_w, t * 16 + j1));
+        }
         dit_regs<Ax, 16>(ar, x, P.rci);
         word* o = base + static_cast<long long>(r0 + r) * kDLine + j1;
 #pragma unroll
