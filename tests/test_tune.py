@@ -24,9 +24,15 @@ def test_tune_rejects_bad_shapes():
 
 def test_default_shapes():
     G.ntt_tune_reset()
-    # one-block sizes: 16 products per block for short vectors, 1 for tiles
+    # one-block sizes: 16 products per block for short vectors, 8 / 4 / 2 for
+    # tiles of 2^9 / 2^10 / 2^11 words (a block's column phase runs at least
+    # 512 lines), 1 from 2^12 on
     assert G.ntt_tune_get(4, 8)[0] == 4
-    assert G.ntt_tune_get(8, 12)[0] == 0
+    for wb in (4, 8):
+        assert [G.ntt_tune_get(wb, k)[0] for k in (9, 10, 11, 12, 13)] == [3, 2, 1, 0, 0]
+    # the one-block limit is 2^13 for both word sizes: 2^14 takes the two
+    # global passes (columns per block logw >= 1)
+    assert G.ntt_tune_get(4, 14)[1] >= 1 and G.ntt_tune_get(8, 14)[1] >= 1
     # n = 2^16 .. 2^24 above the one-block limit: the direct kernels (logw = 0)
     for k in range(16, 25):
         assert G.ntt_tune_get(4, k)[1] == 0 and G.ntt_tune_get(8, k)[1] == 0
