@@ -159,9 +159,11 @@ size_t polymul_workspace_size(const ntt_plan* plan, size_t batch, unsigned sched
  * back to back.  Requires 1 <= na, nb and na + nb - 1 <= n: the product is
  * the size-n cyclic convolution of the zero-padded operands, which equals the
  * linear product when no coefficient wraps.  Two forward transforms, the
- * pointwise product and one inverse transform (Section 5.2); for n = 2^16 ..
- * 2^24 the transforms are truncated (TFT, Section 5.1) to the rows that the
- * na + nb - 1 output words need, which changes nothing in c.  schedule:
+ * pointwise product and one inverse transform (Section 5.2).  From n = 2^9
+ * on, the transforms are truncated (TFT, Section 5.1) to the blocks of
+ * n/16 positions (rows of 2^16 words above 2^16 points) that the na + nb - 1
+ * output words need, wherever that measured faster; this changes nothing in
+ * c.  schedule:
  * NTT_SCHED_FUSED or NTT_SCHED_PLAIN (the latter needs NTT_FLAG_PLAIN).
  * d_ws: at least polymul_workspace_size bytes, 256-byte aligned (may be
  * NULL when that size is 0). */
@@ -261,8 +263,10 @@ typedef struct polymul_batch_plan polymul_batch_plan;
  * product's transform length is the least 2^k >= na + nb - 1.  Products
  * with 2^k within one thread block become items of a persistent kernel
  * that takes them from a ticket counter (largest first, up to 16 equal-size
- * equal-modulus products per item); longer products are grouped by
- * (modulus, k) and run as the fused three-pass schedule.  Allocates the
+ * equal-modulus products per item, items truncated to the blocks their
+ * longest output needs); longer products are grouped by (modulus, k, and
+ * below 2^16 points whether truncation pays) and run as the fused three-pass
+ * schedule, each product truncated to its own output length.  Allocates the
  * transform plans and the device descriptor tables (not a hot call).
  * flags: reserved, pass 0. */
 int polymul_batch_plan_create(const uint64_t* primes, unsigned nprimes, const polymul_desc* h_desc,
