@@ -42,8 +42,13 @@ __host__ __device__ constexpr size_t cluster_smem_words() {
     return size_t(2) * 64 * kClS + size_t(2) * 8 * kClR + size_t(8) * kClR + size_t(64) * kClS;
 }
 
-__device__ __forceinline__ void cluster_arrive_release() {
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+// Arrival without a release fence: used only to say "this CTA reads no other
+// CTA's shared memory any more".  Every remote load a thread made before it
+// has returned (its value was consumed by the stores that precede the
+// arrival), and the CTA's later writes are read by no other CTA, so there is
+// nothing to order.
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void cluster_wait_acquire() {
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -206,7 +211,7 @@ k_cluster_polymul(DevPlan<Ar> P, const typename WideForm<Ar>::type ar, const typ
 #pragma unroll
         for (int u = 0; u < 8; ++u) S2[(8 * tp + u) * kClS + cl] = x[u];
     }
-    cluster_arrive_release();          // this CTA reads no other CTA's memory from here on
+    cluster_arrive_relaxed();          // this CTA reads no other CTA's memory from here on
     __syncthreads();
     // inverse of the column phase's first pass, scaled store: thread
     // (column 8q + lo, split column hi)
